@@ -1,0 +1,178 @@
+/*
+ * ipm.h -- exact dense integer polynomial multiplication on one GB300 GPU.
+ *
+ * Method: "Parallel Integer Polynomial Multiplication" (Chen, Covanov,
+ * Mansouri, Moreno Maza, Xie, Xie; arXiv 1612.05778), in the form its §4
+ * implements (several machine-word Fourier primes and Chinese remaindering,
+ * "CVL_p^2"):
+ *
+ *   1. DetermineBase (§2): N = K*M, beta = 2^M, K a power of two.
+ *   2. BivariateRepresentation (§2): every coefficient a_i becomes
+ *      sum_{j<K} a_{i,j} beta^j with balanced digits a_{i,j}.
+ *   3. CyclicConvolution / NegacyclicConvolution (§2.1): C^-(x,y) = A*B
+ *      mod (x^K - 1) and C^+(x,y) = A*B mod (x^K + 1), by two-dimensional
+ *      number-theoretic transforms over each prime p_t (the negacyclic one
+ *      after the twist x -> theta*x, theta a primitive 2K-th root of unity).
+ *   4. Chinese remaindering over the primes (§4) of the per-digit values
+ *      c_{i,j} = (c^-_{i,j} + c^+_{i,j})/2 and c_{i,j+K} = (c^-_{i,j} -
+ *      c^+_{i,j})/2, which is RecoveringProduct's step 3 (§2.2) written per
+ *      digit, then the shift-and-add c_i = sum_j c_{i,j} 2^{Mj} with carry
+ *      propagation.
+ *
+ * Number format (§2.3 stores coefficient i of a in words [i*ceil(N/w),
+ * (i+1)*ceil(N/w)); here w = 32 and magnitudes are sign-magnitude):
+ *   - coefficient i of a occupies 32-bit little-endian limbs
+ *     a[i*La .. (i+1)*La) holding |a_i|, La = ceil(bits_a / 32);
+ *   - a_neg[i] is 1 when a_i < 0 and 0 otherwise (-0 is accepted);
+ *   - |a_i| < 2^bits_a is required (checked on the device: IPM_ERR_BOUND);
+ *   - the product c has (deg_a + deg_b + 1) coefficients with stride
+ *     Lc = ceil((bits_a + bits_b + ceil(log2(min(deg_a, deg_b) + 1))) / 32)
+ *     limbs (ipm_plan_info.lc); output zero always has c_neg = 0 and every
+ *     limb above a coefficient's magnitude is written as 0.
+ *
+ * Ownership: the caller owns every operand buffer.  A plan owns its
+ * device workspace and tables.  Calls on a plan are ordered on the stream
+ * given and are asynchronous unless IPM_SYNC is set; one plan must not be
+ * used by two calls that overlap in time (they share the workspace).
+ *
+ * Errors: argument errors are returned at once.  Errors found on the device
+ * (an input above its bit bound) are recorded in a per-plan device word and
+ * returned by ipm_sync(), or by the call itself when IPM_SYNC is set.
+ * Nothing is ever reported by trapping the GPU.
+ */
+#ifndef IPM_H
+#define IPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ipm_plan_s *ipm_plan_t;
+
+/* A CUDA stream (cudaStream_t); NULL is the legacy default stream. */
+typedef void *ipm_stream_t;
+
+typedef enum {
+    IPM_OK = 0,
+    IPM_ERR_ARG = 1,          /* invalid argument or shape */
+    IPM_ERR_BOUND = 2,        /* an input coefficient is >= 2^bits */
+    IPM_ERR_NOMEM = 3,        /* device or host allocation failed */
+    IPM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    IPM_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
+    IPM_ERR_UNSUPPORTED = 6   /* shape outside what the plan tables support */
+} ipm_status;
+
+/* Plan flags. */
+#define IPM_SYNC 1u           /* calls synchronise and return device errors */
+
+/* One product shape: a has deg_a+1 coefficients with |a_i| < 2^bits_a. */
+typedef struct {
+    int64_t deg_a, deg_b;
+    uint32_t bits_a, bits_b;  /* 1 .. 65536 */
+} ipm_shape;
+
+/*
+ * Optional overrides of the planner's choices (0 = let the planner choose).
+ * Every valid choice gives the same exact product.
+ *   K : number of base-2^M digits per coefficient (power of two, 2..2048)
+ *   M : digit width in bits (2..62); needs K*M >= max(bits_a,bits_b)+1
+ *   r : number of 30-bit Fourier primes (1..6); needs prod p > 4H (§2.1)
+ *   y2: rows per forward/inverse tile (power of two dividing Y)
+ *   s : columns per middle-pass tile (power of two dividing 2K)
+ */
+typedef struct {
+    int32_t K, M, r, y2, s;
+} ipm_params;
+
+/* What a plan chose (ipm_choose / ipm_get_info). */
+typedef struct {
+    int64_t na, nb, nc;       /* coefficient counts of a, b and c */
+    int32_t la, lb, lc;       /* limb strides of a, b and c */
+    int32_t K, M, N, r;       /* split N = K*M and number of primes */
+    int64_t Y, Y1, Y2;        /* y-transform length Y = Y1*Y2 >= nc */
+    int32_t S;                /* middle-pass column slice */
+    uint32_t primes[8];       /* p_0 > p_1 > ... (r used) */
+    double log2_modulus;      /* log2(prod p) */
+    double log2_bound;        /* log2(4H), H = min(na,nb)*K*2^(2M-2) */
+    size_t workspace_bytes;   /* device bytes the plan allocates */
+} ipm_plan_info;
+
+/*
+ * Host-only planner (DetermineBase and RecoveryPrime, §2 and §2.1; the
+ * prime-product form of §4).  Touches no GPU.  `params` may be NULL.
+ * Returns IPM_ERR_ARG for an invalid shape or override and
+ * IPM_ERR_UNSUPPORTED when no plan meets the bounds.
+ */
+ipm_status ipm_choose(const ipm_shape *shape, const ipm_params *params, ipm_plan_info *out);
+
+/*
+ * Create a plan for n product shapes on the current CUDA device: runs the
+ * planner, builds the twiddle/CRT tables and allocates the workspace.
+ * n = 1 for ipm_mul; n >= 1 for ipm_mul_batched (the i-th operand set of a
+ * batched call must match shapes[i]).  `params` (may be NULL) applies to
+ * every shape.  On success *out receives the plan; on failure *out = NULL.
+ */
+ipm_status ipm_plan(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint32_t flags);
+ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint32_t flags,
+                       const ipm_params *params);
+
+/* Plan parameters of shape `index` of a plan. */
+ipm_status ipm_get_info(ipm_plan_t plan, int32_t index, ipm_plan_info *out);
+
+/*
+ * c = a*b (§2.3, lines 1-8 of the main algorithm) for a plan with n = 1.
+ * a, a_neg, b, b_neg, c, c_neg are DEVICE pointers in the format above,
+ * 16-byte aligned for the limb arrays.  c must not overlap a or b.
+ */
+ipm_status ipm_mul(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg,
+                   const uint32_t *b, const uint8_t *b_neg,
+                   uint32_t *c, uint8_t *c_neg, ipm_stream_t stream);
+
+/*
+ * Same product with HOST buffers (pinned memory is fastest): copies a and b
+ * to plan-owned device buffers, multiplies, copies c back and waits for the
+ * stream.  The device buffers are allocated on first use and kept.
+ */
+ipm_status ipm_mul_host(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg,
+                        const uint32_t *b, const uint8_t *b_neg,
+                        uint32_t *c, uint8_t *c_neg, ipm_stream_t stream);
+
+/* Device pointers of one product of a batch (layout as for ipm_mul). */
+typedef struct {
+    const uint32_t *a;
+    const uint8_t *a_neg;
+    const uint32_t *b;
+    const uint8_t *b_neg;
+    uint32_t *c;
+    uint8_t *c_neg;
+} ipm_operands;
+
+/*
+ * n independent products ops[i] with shapes[i] of the plan (n must equal
+ * the plan's shape count).  `ops` is a HOST array of device pointers.
+ * Products run one after another on `stream` (§2.4 parallelises within a
+ * product; so does every kernel here).
+ */
+ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n,
+                           ipm_stream_t stream);
+
+/* Wait for `stream`, then return and clear the plan's device error word. */
+ipm_status ipm_sync(ipm_plan_t plan, ipm_stream_t stream);
+
+/* Free a plan (waits for the device first).  NULL is accepted. */
+ipm_status ipm_destroy(ipm_plan_t plan);
+
+/* Static description of a status code. */
+const char *ipm_strerror(ipm_status status);
+
+/* Number of kernels this library has launched in this process. */
+int64_t ipm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPM_H */

@@ -1,0 +1,250 @@
+"""Exact dense Z[y] multiplication on GB300 (arXiv 1612.05778, CVL_p^2 form).
+
+A thin ctypes binding over the C ABI of ``include/ipm.h`` (``libipm.so``,
+built in-tree by ``paper_1612_05778_gb300.build``).  It only marshals
+arguments: every step of a product runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  There is no CPU fallback: if
+the library is missing, importing the binding's entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libipm.so")
+
+IPM_SYNC = 1
+
+STATUS = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_BOUND", 3: "IPM_ERR_NOMEM",
+          4: "IPM_ERR_CUDA", 5: "IPM_ERR_TIMEOUT", 6: "IPM_ERR_UNSUPPORTED"}
+
+
+class IpmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s (%d)" % (what, STATUS.get(status, "?"), status))
+        self.status = status
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("deg_a", ctypes.c_int64), ("deg_b", ctypes.c_int64),
+                ("bits_a", ctypes.c_uint32), ("bits_b", ctypes.c_uint32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("M", ctypes.c_int32), ("r", ctypes.c_int32),
+                ("y2", ctypes.c_int32), ("s", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("na", ctypes.c_int64), ("nb", ctypes.c_int64), ("nc", ctypes.c_int64),
+                ("la", ctypes.c_int32), ("lb", ctypes.c_int32), ("lc", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("M", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("r", ctypes.c_int32), ("Y", ctypes.c_int64), ("Y1", ctypes.c_int64),
+                ("Y2", ctypes.c_int64), ("S", ctypes.c_int32), ("primes", ctypes.c_uint32 * 8),
+                ("log2_modulus", ctypes.c_double), ("log2_bound", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "primes"}
+        d["primes"] = [int(self.primes[i]) for i in range(self.r)]
+        return d
+
+
+class Operands(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_void_p), ("a_neg", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("b_neg", ctypes.c_void_p), ("c", ctypes.c_void_p), ("c_neg", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libipm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libipm.so is missing (%s): run paper_1612_05778_gb300.build.build()" % p)
+    lib = ctypes.CDLL(p)
+    V, I32, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32
+    lib.ipm_choose.argtypes = [ctypes.POINTER(Shape), ctypes.POINTER(Params), ctypes.POINTER(PlanInfo)]
+    lib.ipm_plan.argtypes = [ctypes.POINTER(V), ctypes.POINTER(Shape), I32, U32]
+    lib.ipm_plan_ex.argtypes = [ctypes.POINTER(V), ctypes.POINTER(Shape), I32, U32, ctypes.POINTER(Params)]
+    lib.ipm_get_info.argtypes = [V, I32, ctypes.POINTER(PlanInfo)]
+    lib.ipm_mul.argtypes = [V, V, V, V, V, V, V, V]
+    lib.ipm_mul_host.argtypes = [V, V, V, V, V, V, V, V]
+    lib.ipm_mul_batched.argtypes = [V, ctypes.POINTER(Operands), I32, V]
+    lib.ipm_sync.argtypes = [V, V]
+    lib.ipm_destroy.argtypes = [V]
+    lib.ipm_strerror.argtypes = [ctypes.c_int]
+    lib.ipm_strerror.restype = ctypes.c_char_p
+    lib.ipm_launch_count.restype = ctypes.c_int64
+    for name in ("ipm_choose", "ipm_plan", "ipm_plan_ex", "ipm_get_info", "ipm_mul", "ipm_mul_host",
+                 "ipm_mul_batched", "ipm_sync", "ipm_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise IpmError(st, what)
+
+
+def _params(K=0, M=0, r=0, y2=0, s=0):
+    if not (K or M or r or y2 or s):
+        return None
+    return Params(K, M, r, y2, s)
+
+
+def choose(na: int, nb: int, bits_a: int, bits_b: int, **overrides) -> dict:
+    """Host-only planner query (no GPU): the plan ipm_plan would build."""
+    lib = load_library()
+    info = PlanInfo()
+    prm = _params(**overrides)
+    _check(lib.ipm_choose(ctypes.byref(Shape(na - 1, nb - 1, bits_a, bits_b)),
+                          ctypes.byref(prm) if prm else None, ctypes.byref(info)), "ipm_choose")
+    return info.as_dict()
+
+
+def launch_count() -> int:
+    return int(load_library().ipm_launch_count())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _dptr(t, dtype, shape=None):
+    import torch
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor of %s" % dtype)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A plan for products of fixed shapes (one shape for mul, several for
+    mul_batched).  Each shape is (na, nb, bits_a, bits_b) with na, nb the
+    coefficient counts; limb tensors are int32 views of the uint32 limbs
+    (torch has no uint32 arithmetic; the bits are what matter)."""
+
+    def __init__(self, shapes, flags: int = 0, **overrides):
+        lib = load_library()
+        if isinstance(shapes, tuple):
+            shapes = [shapes]
+        arr = (Shape * len(shapes))(*[Shape(na - 1, nb - 1, ba, bb) for na, nb, ba, bb in shapes])
+        prm = _params(**overrides)
+        h = ctypes.c_void_p()
+        _check(lib.ipm_plan_ex(ctypes.byref(h), arr, len(shapes), flags,
+                               ctypes.byref(prm) if prm else None), "ipm_plan")
+        self._h = h
+        self._lib = lib
+        self.shapes = list(shapes)
+        self.infos = []
+        for i in range(len(shapes)):
+            info = PlanInfo()
+            _check(lib.ipm_get_info(h, i, ctypes.byref(info)), "ipm_get_info")
+            self.infos.append(info.as_dict())
+
+    @property
+    def info(self) -> dict:
+        return self.infos[0]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.ipm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty_output(self, index: int = 0):
+        import torch
+        I = self.infos[index]
+        return (torch.empty((I["nc"], I["lc"]), dtype=torch.int32, device="cuda"),
+                torch.empty((I["nc"],), dtype=torch.uint8, device="cuda"))
+
+    def mul(self, a, a_neg, b, b_neg, c=None, c_neg=None, stream=None):
+        """c = a*b on the device; tensors: limbs int32 (n, L), signs uint8 (n,)."""
+        import torch
+        I = self.info
+        if c is None or c_neg is None:
+            c, c_neg = self.empty_output()
+        args = [_dptr(a, torch.int32, (I["na"], I["la"])), _dptr(a_neg, torch.uint8, (I["na"],)),
+                _dptr(b, torch.int32, (I["nb"], I["lb"])), _dptr(b_neg, torch.uint8, (I["nb"],)),
+                _dptr(c, torch.int32, (I["nc"], I["lc"])), _dptr(c_neg, torch.uint8, (I["nc"],))]
+        _check(self._lib.ipm_mul(self._h, *args, _stream_handle(stream)), "ipm_mul")
+        return c, c_neg
+
+    def mul_host(self, a: np.ndarray, a_neg: np.ndarray, b: np.ndarray, b_neg: np.ndarray,
+                 c: np.ndarray | None = None, c_neg: np.ndarray | None = None, stream=None):
+        """c = a*b with host (numpy) buffers; waits for the result."""
+        I = self.info
+        a = np.ascontiguousarray(a, dtype=np.uint32)
+        b = np.ascontiguousarray(b, dtype=np.uint32)
+        a_neg = np.ascontiguousarray(a_neg, dtype=np.uint8)
+        b_neg = np.ascontiguousarray(b_neg, dtype=np.uint8)
+        if a.shape != (I["na"], I["la"]) or b.shape != (I["nb"], I["lb"]):
+            raise ValueError("operand shapes do not match the plan")
+        if c is None:
+            c = np.empty((I["nc"], I["lc"]), dtype=np.uint32)
+        if c_neg is None:
+            c_neg = np.empty((I["nc"],), dtype=np.uint8)
+        P = lambda x: ctypes.c_void_p(x.ctypes.data)  # noqa: E731
+        _check(self._lib.ipm_mul_host(self._h, P(a), P(a_neg), P(b), P(b_neg), P(c), P(c_neg),
+                                      _stream_handle(stream)), "ipm_mul_host")
+        return c, c_neg
+
+    def mul_batched(self, operands, outputs=None, stream=None):
+        """operands: list of (a, a_neg, b, b_neg) device tensors matching the
+        plan's shapes; returns the list of (c, c_neg)."""
+        import torch
+        n = len(self.shapes)
+        if len(operands) != n:
+            raise ValueError("need one operand set per plan shape")
+        if outputs is None:
+            outputs = [self.empty_output(i) for i in range(n)]
+        arr = (Operands * n)()
+        for i, ((a, an, b, bn), (c, cn)) in enumerate(zip(operands, outputs)):
+            I = self.infos[i]
+            arr[i] = Operands(_dptr(a, torch.int32, (I["na"], I["la"])).value,
+                              _dptr(an, torch.uint8, (I["na"],)).value,
+                              _dptr(b, torch.int32, (I["nb"], I["lb"])).value,
+                              _dptr(bn, torch.uint8, (I["nb"],)).value,
+                              _dptr(c, torch.int32, (I["nc"], I["lc"])).value,
+                              _dptr(cn, torch.uint8, (I["nc"],)).value)
+        _check(self._lib.ipm_mul_batched(self._h, arr, n, _stream_handle(stream)), "ipm_mul_batched")
+        return outputs
+
+    def sync(self, stream=None):
+        """Wait for the stream and raise on a device-side error (e.g. IPM_ERR_BOUND)."""
+        _check(self._lib.ipm_sync(self._h, _stream_handle(stream)), "ipm_sync")
+
+
+def to_device(limbs: np.ndarray, neg: np.ndarray):
+    """numpy (uint32 limbs, uint8 signs) -> CUDA tensors (int32 view, uint8)."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(limbs, dtype=np.uint32).view(np.int32)).cuda()
+    s = torch.from_numpy(np.ascontiguousarray(neg, dtype=np.uint8)).cuda()
+    return t, s
+
+
+def to_host(c, c_neg):
+    """CUDA tensors -> numpy (uint32 limbs, uint8 signs)."""
+    return (c.cpu().numpy().view(np.uint32), c_neg.cpu().numpy())
+
+
+__all__ = ["Plan", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
+           "IPM_SYNC", "LIB_PATH"]

@@ -1,0 +1,229 @@
+// ipm_api.cu -- the C ABI of include/ipm.h.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "ipm_internal.h"
+
+using namespace ipm;
+
+struct ipm_plan_s {
+    int device = 0;
+    uint32_t flags = 0;
+    std::vector<ShapePlan> shapes;
+    std::vector<void *> allocations;  // device allocations owned by the plan
+    uint32_t *Z = nullptr;            // shared workspace (largest shape)
+    int *err = nullptr;               // device error word
+    // ipm_mul_host staging (allocated on first use)
+    unsigned char *io = nullptr;
+    size_t io_bytes = 0;
+};
+
+namespace {
+
+ipm_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return IPM_OK;
+    if (e == cudaErrorMemoryAllocation) return IPM_ERR_NOMEM;
+    return IPM_ERR_CUDA;
+}
+
+void free_plan(ipm_plan_s *p) {
+    if (!p) return;
+    for (void *ptr : p->allocations) cudaFree(ptr);
+    delete p;
+}
+
+bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+ipm_status run_one(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a, const uint8_t *an,
+                   const uint32_t *b, const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream) {
+    if (!a || !an || !b || !bn || !c || !cn) return IPM_ERR_ARG;
+    if (!aligned16(a) || !aligned16(b) || !aligned16(c)) return IPM_ERR_ARG;
+    if (launch_forward(sp.kp, sp.smem_fwd, a, an, b, bn, stream)) return IPM_ERR_CUDA;
+    if (launch_middle(sp.kp, sp.smem_mid, stream)) return IPM_ERR_CUDA;
+    if (launch_inverse(sp.kp, sp.smem_inv, c, cn, stream)) return IPM_ERR_CUDA;
+    (void)plan;
+    return IPM_OK;
+}
+
+ipm_status read_error(ipm_plan_s *plan, void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int h = 0;
+    e = cudaMemcpy(&h, plan->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (h) {
+        e = cudaMemset(plan->err, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_status(e);
+        if (h & ERRBIT_BOUND) return IPM_ERR_BOUND;
+        return IPM_ERR_CUDA;
+    }
+    return IPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint32_t flags,
+                       const ipm_params *params) {
+    if (!out) return IPM_ERR_ARG;
+    *out = nullptr;
+    if (!shapes || n < 1) return IPM_ERR_ARG;
+    ipm_plan_s *plan = new (std::nothrow) ipm_plan_s();
+    if (!plan) return IPM_ERR_NOMEM;
+    plan->flags = flags;
+    cudaError_t ce = cudaGetDevice(&plan->device);
+    if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+    if (set_kernel_attributes()) { free_plan(plan); return IPM_ERR_CUDA; }
+    plan->shapes.resize((size_t)n);
+    size_t zmax = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        ipm_status st = choose_plan(shapes[i], params, plan->shapes[(size_t)i]);
+        if (st != IPM_OK) { free_plan(plan); return st; }
+        zmax = std::max(zmax, plan->shapes[(size_t)i].z_words);
+    }
+    // Tables are shared between shapes with the same (Y, K, r): the primes
+    // are always the r largest of the table, so these fix every entry.
+    std::map<std::tuple<int64_t, int32_t, int32_t>, const uint2 *> cache;
+    for (auto &sp : plan->shapes) {
+        auto key = std::make_tuple(sp.kp.Y, sp.kp.K, sp.kp.r);
+        std::vector<uint2> host((size_t)sp.kp.r * sp.table_words);
+        build_tables(sp, host.data());  // also fills the scalar constants
+        const uint2 *dtab = nullptr;
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            dtab = it->second;
+        } else {
+            void *d = nullptr;
+            ce = cudaMalloc(&d, host.size() * sizeof(uint2));
+            if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+            plan->allocations.push_back(d);
+            ce = cudaMemcpy(d, host.data(), host.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+            dtab = (const uint2 *)d;
+            cache[key] = dtab;
+        }
+        const TableLayout L = table_layout(sp.kp.Y, sp.kp.K);
+        for (int t = 0; t < sp.kp.r; ++t) {
+            const uint2 *blk = dtab + (size_t)t * L.total;
+            sp.kp.pc[t].ty_f = blk + L.ty_f;
+            sp.kp.pc[t].ty_i = blk + L.ty_i;
+            sp.kp.pc[t].tx_f = blk + L.tx_f;
+            sp.kp.pc[t].tx_i = blk + L.tx_i;
+            sp.kp.pc[t].untw = blk + L.untw;
+        }
+    }
+    void *d = nullptr;
+    ce = cudaMalloc(&d, zmax * sizeof(uint32_t));
+    if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+    plan->allocations.push_back(d);
+    plan->Z = (uint32_t *)d;
+    ce = cudaMalloc(&d, 16);
+    if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+    plan->allocations.push_back(d);
+    plan->err = (int *)d;
+    ce = cudaMemset(plan->err, 0, 16);
+    if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+    for (auto &sp : plan->shapes) {
+        sp.kp.Z = plan->Z;
+        sp.kp.err = plan->err;
+    }
+    *out = plan;
+    return IPM_OK;
+}
+
+ipm_status ipm_plan(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint32_t flags) {
+    return ipm_plan_ex(out, shapes, n, flags, nullptr);
+}
+
+ipm_status ipm_get_info(ipm_plan_t plan, int32_t index, ipm_plan_info *out) {
+    if (!plan || !out || index < 0 || (size_t)index >= plan->shapes.size()) return IPM_ERR_ARG;
+    *out = plan->shapes[(size_t)index].info;
+    return IPM_OK;
+}
+
+ipm_status ipm_mul(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg, const uint32_t *b,
+                   const uint8_t *b_neg, uint32_t *c, uint8_t *c_neg, ipm_stream_t stream) {
+    if (!plan || plan->shapes.size() != 1) return IPM_ERR_ARG;
+    ipm_status st = run_one(plan, plan->shapes[0], a, a_neg, b, b_neg, c, c_neg, stream);
+    if (st != IPM_OK) return st;
+    if (plan->flags & IPM_SYNC) return read_error(plan, stream);
+    return IPM_OK;
+}
+
+ipm_status ipm_mul_host(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg, const uint32_t *b,
+                        const uint8_t *b_neg, uint32_t *c, uint8_t *c_neg, ipm_stream_t stream) {
+    if (!plan || plan->shapes.size() != 1) return IPM_ERR_ARG;
+    if (!a || !a_neg || !b || !b_neg || !c || !c_neg) return IPM_ERR_ARG;
+    const ipm_plan_info &I = plan->shapes[0].info;
+    auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t ba = (size_t)I.na * I.la * 4, bb = (size_t)I.nb * I.lb * 4, bc = (size_t)I.nc * I.lc * 4;
+    const size_t oa = 0, oan = oa + up16(ba), ob = oan + up16((size_t)I.na), obn = ob + up16(bb),
+                 oc = obn + up16((size_t)I.nb), ocn = oc + up16(bc), total = ocn + up16((size_t)I.nc);
+    if (!plan->io) {
+        void *d = nullptr;
+        cudaError_t ce = cudaMalloc(&d, total);
+        if (ce != cudaSuccess) return cuda_status(ce);
+        plan->allocations.push_back(d);
+        plan->io = (unsigned char *)d;
+        plan->io_bytes = total;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char *io = plan->io;
+    cudaError_t ce;
+    if ((ce = cudaMemcpyAsync(io + oa, a, ba, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(ce);
+    if ((ce = cudaMemcpyAsync(io + oan, a_neg, (size_t)I.na, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(ce);
+    if ((ce = cudaMemcpyAsync(io + ob, b, bb, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(ce);
+    if ((ce = cudaMemcpyAsync(io + obn, b_neg, (size_t)I.nb, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(ce);
+    ipm_status st = run_one(plan, plan->shapes[0], (const uint32_t *)(io + oa), io + oan,
+                            (const uint32_t *)(io + ob), io + obn, (uint32_t *)(io + oc), io + ocn, stream);
+    if (st != IPM_OK) return st;
+    if ((ce = cudaMemcpyAsync(c, io + oc, bc, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_status(ce);
+    if ((ce = cudaMemcpyAsync(c_neg, io + ocn, (size_t)I.nc, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_status(ce);
+    return read_error(plan, stream);
+}
+
+ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n, ipm_stream_t stream) {
+    if (!plan || !ops || n < 0 || (size_t)n != plan->shapes.size()) return IPM_ERR_ARG;
+    for (int32_t i = 0; i < n; ++i) {
+        const ipm_operands &o = ops[i];
+        ipm_status st = run_one(plan, plan->shapes[(size_t)i], o.a, o.a_neg, o.b, o.b_neg, o.c, o.c_neg, stream);
+        if (st != IPM_OK) return st;
+    }
+    if (plan->flags & IPM_SYNC) return read_error(plan, stream);
+    return IPM_OK;
+}
+
+ipm_status ipm_sync(ipm_plan_t plan, ipm_stream_t stream) {
+    if (!plan) return IPM_ERR_ARG;
+    return read_error(plan, stream);
+}
+
+ipm_status ipm_destroy(ipm_plan_t plan) {
+    if (!plan) return IPM_OK;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return IPM_OK;
+}
+
+const char *ipm_strerror(ipm_status s) {
+    switch (s) {
+        case IPM_OK: return "ok";
+        case IPM_ERR_ARG: return "invalid argument";
+        case IPM_ERR_BOUND: return "input coefficient exceeds its bit bound";
+        case IPM_ERR_NOMEM: return "out of memory";
+        case IPM_ERR_CUDA: return "CUDA error";
+        case IPM_ERR_TIMEOUT: return "device wait timed out";
+        case IPM_ERR_UNSUPPORTED: return "shape not supported";
+    }
+    return "unknown status";
+}
+
+int64_t ipm_launch_count(void) { return launches_so_far(); }
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// ipm_internal.h -- plan parameters shared by the host planner and kernels.
+#pragma once
+#include <stdint.h>
+#include <stddef.h>
+#include <cuda_runtime.h>
+
+#include "../../include/ipm.h"
+
+namespace ipm {
+
+constexpr int RMAX = 6;              // most Fourier primes a plan may use
+constexpr int PRIME_ORDER_LOG2 = 21; // every prime p satisfies 2^21 | p - 1
+constexpr int KMAX_LOG2 = 11;        // K <= 2048 digits per coefficient
+constexpr int MMAX = 62;             // digit width, |digit| <= 2^(M-1) < 2^63
+
+// Tile budgets (bytes of dynamic shared memory).
+constexpr size_t SMEM_FWD_MAX = 100 * 1024;
+constexpr size_t SMEM_INV_MAX = 112 * 1024;
+constexpr size_t SMEM_MID_MAX = 200 * 1024;
+
+constexpr int THREADS_FWD = 256;
+constexpr int THREADS_MID = 512;
+constexpr int THREADS_INV = 256;
+
+// Device error word bits.
+constexpr int ERRBIT_BOUND = 1;      // an input coefficient >= 2^bits
+constexpr int ERRBIT_INTERNAL = 2;   // recombination top limb not a sign word
+
+// Bytes of per-warp recombination staging in the inverse pass: lc+1
+// limbs (u32) plus lc+1 carry bytes, rounded up to 16.
+__host__ __device__ inline size_t stage_bytes_per_warp(int lc) {
+    return (((size_t)lc + 1) * 5 + 15) & ~(size_t)15;
+}
+
+// Per-prime constants.  Twiddle tables hold (w, floor(w * 2^32 / p)) pairs
+// for Shoup's precomputed-quotient multiplication.
+struct PrimeConst {
+    uint32_t p;        // prime, 2^29 < p < 2^30, p = 1 mod 2^21
+    uint32_t p2;       // 2p
+    uint32_t mont;     // -p^{-1} mod 2^32 (Montgomery REDC)
+    uint32_t one_s;    // floor(2^32 / p): Shoup quotient of w = 1
+    uint32_t c32;      // 2^32 mod p
+    uint32_t c32_s;    // its Shoup quotient
+    uint32_t scale;    // 2^32 * (2 Y K)^{-1} mod p (inverse-transform scale)
+    uint32_t scale_s;
+    const uint2 *ty_f; // omega_Y^e,     e < Y   (forward y twiddles)
+    const uint2 *ty_i; // omega_Y^{-e},  e < Y   (inverse y twiddles)
+    const uint2 *tx_f; // theta^e,       e < 2K  (theta: primitive 2K-th root)
+    const uint2 *tx_i; // theta^{-e},    e < 2K
+    const uint2 *untw; // scale * theta^{-j}, j < K
+};
+
+// Everything one product needs on the device (passed by value, < 4 KB).
+struct KParams {
+    int64_t na, nb, nc;   // coefficient counts of a, b, c
+    int32_t la, lb, lc;   // limb strides
+    uint32_t bits_a, bits_b;
+    int32_t K, logK, M, N, r;
+    int64_t Y, Y1, Y2;
+    int32_t logY, logY1, logY2, S, logS;
+    PrimeConst pc[RMAX];
+    // Garner: ginv[t][s] = p_s^{-1} mod p_t (s < t), with Shoup quotients.
+    uint32_t ginv[RMAX][RMAX];
+    uint32_t ginv_s[RMAX][RMAX];
+    // m = prod p_t as r little-endian 32-bit words (fits: each p < 2^30).
+    uint32_t m_words[RMAX];
+    uint32_t *Z;          // workspace: r x 2 x Y x 2K words
+    int *err;             // device error word
+};
+
+// Host-side plan record for one shape.
+struct ShapePlan {
+    ipm_plan_info info;
+    KParams kp;           // pointers filled in by ipm_plan
+    size_t smem_fwd, smem_mid, smem_inv;
+    size_t z_words;       // workspace words
+    size_t table_words;   // table uint2 entries per prime
+};
+
+// Planner (host only).  Fills sp (minus device pointers) or returns an error.
+ipm_status choose_plan(const ipm_shape &shape, const ipm_params *params, ShapePlan &sp);
+
+// Builds the per-prime tables for sp into host memory `tab` (r blocks of
+// sp.table_words uint2 entries) and fills the scalar constants of sp.kp.
+void build_tables(ShapePlan &sp, uint2 *tab);
+
+// Table block offsets (uint2 entries) within one prime's block.
+struct TableLayout {
+    size_t ty_f, ty_i, tx_f, tx_i, untw, total;
+};
+TableLayout table_layout(int64_t Y, int32_t K);
+
+// Kernel launchers (ipm_kernels.cu).
+int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint8_t *an,
+                   const uint32_t *b, const uint8_t *bn, void *stream);
+int launch_middle(const KParams &kp, size_t smem, void *stream);
+int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, void *stream);
+int set_kernel_attributes();
+int64_t launches_so_far();
+
+}  // namespace ipm

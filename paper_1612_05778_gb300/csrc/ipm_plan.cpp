@@ -1,0 +1,374 @@
+// ipm_plan.cpp -- host planner: DetermineBase and RecoveryPrime (§2, §2.1),
+// in the several-word-size-primes form of §4, plus the twiddle and CRT
+// tables the kernels read.
+//
+// Choices (the paper leaves them to table look-up, §2.4):
+//  * K is a power of two (2-way FFTs, §2.1) and N = K*M >= max(bits)+1 so
+//    that every coefficient is an N-bit two's-complement number (Eq.
+//    definingN).  M >= 2 and K >= 2 (Theorem 1 asks K, M > 1).
+//  * The primes p_t satisfy 2^29 < p_t < 2^30 and 2^21 | p_t - 1, so they
+//    hold primitive roots of every power-of-two order up to 2^21 (Eq.
+//    HavingAppropriatePrimitiveRootsOfUnity, with Y = 2^ceil(log2(nc)) in
+//    place of 2d-1 and 2K for theta's order).
+//  * The modulus m = prod p_t must exceed 4H (the m > 4H of §1), with H the
+//    largest |c_{i,j}|.  Digits satisfy |a_{i,j}| <= 2^(M-1), and a
+//    coefficient c_{i,j} sums at most min(na,nb)*K products, so
+//    H <= min(na,nb) * K * 2^(2M-2) and the test is m > min(na,nb)*K*2^(2M).
+//  * Among the valid (K, M, r) the planner takes the cheapest by a simple
+//    work estimate: r transforms of Y x 2K points (the complexity of §4 has
+//    the same shape, O(dKM log(dK)(log(dK) + 2M))).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ipm_internal.h"
+
+namespace ipm {
+namespace {
+
+uint64_t powmod(uint64_t b, uint64_t e, uint64_t m) {
+    uint64_t r = 1 % m;
+    b %= m;
+    while (e) {
+        if (e & 1) r = r * b % m;
+        b = b * b % m;
+        e >>= 1;
+    }
+    return r;
+}
+
+// Deterministic Miller-Rabin for n < 4,759,123,141 (bases 2, 7, 61).
+bool is_prime32(uint64_t n) {
+    if (n < 2) return false;
+    for (uint64_t q : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 61ull})
+        if (n % q == 0) return n == q;
+    uint64_t d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) { d >>= 1; ++s; }
+    for (uint64_t a : {2ull, 7ull, 61ull}) {
+        uint64_t x = powmod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int i = 1; i < s; ++i) {
+            x = x * x % n;
+            if (x == n - 1) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+// Primes p = c*2^21 + 1 with 2^29 < p < 2^30, largest first.
+const std::vector<uint32_t> &prime_table() {
+    static std::vector<uint32_t> table;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (uint64_t c = (1ull << (30 - PRIME_ORDER_LOG2)) - 1; c >= (1ull << (29 - PRIME_ORDER_LOG2)); --c) {
+            uint64_t p = (c << PRIME_ORDER_LOG2) + 1;
+            if (p < (1ull << 30) && p > (1ull << 29) && is_prime32(p)) table.push_back((uint32_t)p);
+        }
+    });
+    return table;
+}
+
+// A generator of (Z/p)^*: g with g^((p-1)/q) != 1 for every prime q | p-1.
+uint32_t generator(uint32_t p) {
+    std::vector<uint64_t> fac;
+    uint64_t n = p - 1;
+    for (uint64_t q = 2; q * q <= n; ++q) {
+        if (n % q == 0) {
+            fac.push_back(q);
+            while (n % q == 0) n /= q;
+        }
+    }
+    if (n > 1) fac.push_back(n);
+    for (uint64_t g = 2;; ++g) {
+        bool ok = true;
+        for (uint64_t q : fac)
+            if (powmod(g, (p - 1) / q, p) == 1) { ok = false; break; }
+        if (ok) return (uint32_t)g;
+    }
+}
+
+// Primitive root of unity of order 2^lg modulo p.
+uint32_t root_of_unity(uint32_t p, int lg) {
+    uint32_t g = generator(p);
+    return (uint32_t)powmod(g, (uint64_t)(p - 1) >> lg, p);
+}
+
+uint32_t shoup_q(uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); }
+uint32_t invmod(uint32_t x, uint32_t p) { return (uint32_t)powmod(x, p - 2, p); }
+
+int ilog2(uint64_t x) {
+    int l = 0;
+    while ((1ull << l) < x) ++l;
+    return l;
+}
+
+// Multiword (little-endian 32-bit) helpers for the exact m > 4H test.
+struct Big {
+    uint32_t w[10];
+};
+Big big_from_u64(uint64_t v) {
+    Big b{};
+    b.w[0] = (uint32_t)v;
+    b.w[1] = (uint32_t)(v >> 32);
+    return b;
+}
+Big big_mul_u32(const Big &a, uint32_t m) {
+    Big r{};
+    uint64_t carry = 0;
+    for (int i = 0; i < 10; ++i) {
+        uint64_t t = (uint64_t)a.w[i] * m + carry;
+        r.w[i] = (uint32_t)t;
+        carry = t >> 32;
+    }
+    return r;
+}
+Big big_shl(const Big &a, int s) {
+    Big r{};
+    int ws = s / 32, bs = s % 32;
+    for (int i = 9; i >= 0; --i) {
+        int src = i - ws;
+        if (src < 0) continue;
+        uint64_t v = (uint64_t)a.w[src] << bs;
+        r.w[i] |= (uint32_t)v;
+        if (i + 1 < 10) r.w[i + 1] |= (uint32_t)(v >> 32);
+    }
+    return r;
+}
+int big_cmp(const Big &a, const Big &b) {
+    for (int i = 9; i >= 0; --i)
+        if (a.w[i] != b.w[i]) return a.w[i] < b.w[i] ? -1 : 1;
+    return 0;
+}
+
+struct Tiles {
+    int64_t Y2;
+    int32_t S;
+    size_t smem_fwd, smem_mid, smem_inv;
+};
+
+size_t fwd_smem(int64_t Y2, int K) { return (size_t)Y2 * K * 8 + (size_t)Y2 * 2 * K * 4; }
+size_t inv_smem(int64_t Y2, int K, int r, int lc) {
+    size_t stage = (size_t)(THREADS_INV / 32) * stage_bytes_per_warp(lc);
+    return (size_t)r * Y2 * 2 * K * 4 + stage;
+}
+size_t mid_smem(int64_t Y1, int S) { return (size_t)2 * Y1 * S * 4; }
+
+// Tile shapes: Y2 rows per forward/inverse tile, S columns per middle tile.
+bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force, Tiles &t) {
+    int64_t y2max = 1;
+    for (int64_t y2 = std::min<int64_t>(Y, 256); y2 >= 1; y2 >>= 1) {
+        if (fwd_smem(y2, K) <= SMEM_FWD_MAX && inv_smem(y2, K, r, lc) <= SMEM_INV_MAX) {
+            y2max = y2;
+            break;
+        }
+        if (y2 == 1) return false;
+    }
+    int64_t Y2 = std::min<int64_t>(y2max, std::max<int64_t>(1, Y / 64));
+    if (y2_force) {
+        if (y2_force > Y || (y2_force & (y2_force - 1)) || fwd_smem(y2_force, K) > SMEM_FWD_MAX ||
+            inv_smem(y2_force, K, r, lc) > SMEM_INV_MAX)
+            return false;
+        Y2 = y2_force;
+    }
+    int64_t Y1 = Y / Y2;
+    int S = 0;
+    for (int s = std::min(2 * K, 32); s >= 1; s >>= 1)
+        if (mid_smem(Y1, s) <= SMEM_MID_MAX) { S = s; break; }
+    if (s_force) {
+        if (s_force > 2 * K || (s_force & (s_force - 1)) || mid_smem(Y1, s_force) > SMEM_MID_MAX)
+            return false;
+        S = s_force;
+    }
+    if (S == 0) return false;
+    t.Y2 = Y2;
+    t.S = S;
+    t.smem_fwd = fwd_smem(Y2, K);
+    t.smem_mid = mid_smem(Y1, S);
+    t.smem_inv = inv_smem(Y2, K, r, lc);
+    return true;
+}
+
+}  // namespace
+
+TableLayout table_layout(int64_t Y, int32_t K) {
+    TableLayout L;
+    L.ty_f = 0;
+    L.ty_i = L.ty_f + (size_t)Y;
+    L.tx_f = L.ty_i + (size_t)Y;
+    L.tx_i = L.tx_f + 2 * (size_t)K;
+    L.untw = L.tx_i + 2 * (size_t)K;
+    L.total = L.untw + (size_t)K;
+    L.total = (L.total + 1) & ~(size_t)1;  // keep blocks 16-byte aligned
+    return L;
+}
+
+ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp) {
+    if (sh.deg_a < 0 || sh.deg_b < 0 || sh.bits_a < 1 || sh.bits_b < 1 ||
+        sh.bits_a > 65536 || sh.bits_b > 65536)
+        return IPM_ERR_ARG;
+    if (sh.deg_a >= (1ll << 40) || sh.deg_b >= (1ll << 40)) return IPM_ERR_UNSUPPORTED;
+    ipm_params P{};
+    if (prm) P = *prm;
+    if (P.K < 0 || P.M < 0 || P.r < 0 || P.y2 < 0 || P.s < 0) return IPM_ERR_ARG;
+    if (P.K && (P.K < 2 || (P.K & (P.K - 1)) || P.K > (1 << KMAX_LOG2))) return IPM_ERR_ARG;
+    if (P.M && (P.M < 2 || P.M > MMAX)) return IPM_ERR_ARG;
+    if (P.r && P.r > RMAX) return IPM_ERR_ARG;
+
+    const int64_t na = sh.deg_a + 1, nb = sh.deg_b + 1, nc = na + nb - 1;
+    const int64_t mn = std::min(na, nb);
+    const uint32_t nmag = std::max(sh.bits_a, sh.bits_b);
+    const int la = (int)((sh.bits_a + 31) / 32), lb = (int)((sh.bits_b + 31) / 32);
+    const int lgmin = ilog2((uint64_t)mn);
+    const int lc = (int)((sh.bits_a + sh.bits_b + (uint32_t)lgmin + 31) / 32);
+    const int logY = ilog2((uint64_t)nc);
+    const int64_t Y = 1ll << logY;
+    if (logY > PRIME_ORDER_LOG2) return IPM_ERR_UNSUPPORTED;
+    const auto &primes = prime_table();
+
+    bool found = false;
+    double best_cost = 0;
+    ShapePlan best{};
+    for (int logK = 1; logK <= KMAX_LOG2; ++logK) {
+        const int K = 1 << logK;
+        if (P.K && K != P.K) continue;
+        if (logK + 1 > PRIME_ORDER_LOG2) continue;
+        int M = (int)((nmag + 1 + K - 1) / K);
+        if (M < 2) M = 2;
+        if (P.M) {
+            if ((int64_t)P.M * K < (int64_t)nmag + 1) continue;
+            M = P.M;
+        }
+        if (M > MMAX) continue;
+        // 4H bound: mn * K * 2^(2M)
+        Big bound = big_shl(big_from_u64((uint64_t)mn * (uint64_t)K), 2 * M);
+        Big m = big_from_u64(1);
+        int r = 0;
+        for (int t = 1; t <= RMAX; ++t) {
+            m = big_mul_u32(m, primes[t - 1]);
+            if (P.r ? t == P.r : big_cmp(m, bound) > 0) {
+                r = t;
+                break;
+            }
+        }
+        if (!r || big_cmp(m, bound) <= 0) continue;
+        Tiles tl;
+        if (!choose_tiles(Y, K, r, lc, P.y2, P.s, tl)) continue;
+        const double pts = (double)r * (double)Y * 2.0 * K;
+        const double cost = pts * (3.0 * (logY + logK + 1) + 2.0 * r + 4.0);
+        if (found && cost >= best_cost) continue;
+        found = true;
+        best_cost = cost;
+        ShapePlan s{};
+        ipm_plan_info &I = s.info;
+        I.na = na; I.nb = nb; I.nc = nc;
+        I.la = la; I.lb = lb; I.lc = lc;
+        I.K = K; I.M = M; I.N = K * M; I.r = r;
+        I.Y = Y; I.Y2 = tl.Y2; I.Y1 = Y / tl.Y2; I.S = tl.S;
+        double lm = 0;
+        for (int t = 0; t < r; ++t) { I.primes[t] = primes[t]; lm += std::log2((double)primes[t]); }
+        I.log2_modulus = lm;
+        I.log2_bound = std::log2((double)mn) + logK + 2.0 * M;
+        s.smem_fwd = tl.smem_fwd;
+        s.smem_mid = tl.smem_mid;
+        s.smem_inv = tl.smem_inv;
+        s.z_words = (size_t)r * 2 * (size_t)Y * 2 * K;
+        s.table_words = table_layout(Y, K).total;
+        I.workspace_bytes = s.z_words * 4 + (size_t)r * s.table_words * 8;
+        KParams &kp = s.kp;
+        std::memset(&kp, 0, sizeof(kp));
+        kp.na = na; kp.nb = nb; kp.nc = nc;
+        kp.la = la; kp.lb = lb; kp.lc = lc;
+        kp.bits_a = sh.bits_a; kp.bits_b = sh.bits_b;
+        kp.K = K; kp.logK = logK; kp.M = M; kp.N = K * M; kp.r = r;
+        kp.Y = Y; kp.Y2 = tl.Y2; kp.Y1 = Y / tl.Y2;
+        kp.logY = logY; kp.logY2 = ilog2((uint64_t)tl.Y2); kp.logY1 = logY - kp.logY2;
+        kp.S = tl.S; kp.logS = ilog2((uint64_t)tl.S);
+        best = s;
+    }
+    if (!found) return (P.K || P.M || P.r || P.y2 || P.s) ? IPM_ERR_ARG : IPM_ERR_UNSUPPORTED;
+    sp = best;
+    return IPM_OK;
+}
+
+void build_tables(ShapePlan &sp, uint2 *tab) {
+    KParams &kp = sp.kp;
+    const int64_t Y = kp.Y;
+    const int K = kp.K;
+    const TableLayout L = table_layout(Y, K);
+    for (int t = 0; t < kp.r; ++t) {
+        const uint32_t p = sp.info.primes[t];
+        uint2 *blk = tab + (size_t)t * L.total;
+        const uint32_t w = root_of_unity(p, kp.logY);          // order Y
+        const uint32_t th = root_of_unity(p, kp.logK + 1);     // order 2K
+        const uint32_t wi = invmod(w, p), thi = invmod(th, p);
+        uint64_t x = 1, xi = 1;
+        for (int64_t e = 0; e < Y; ++e) {
+            blk[L.ty_f + e] = make_uint2((uint32_t)x, shoup_q((uint32_t)x, p));
+            blk[L.ty_i + e] = make_uint2((uint32_t)xi, shoup_q((uint32_t)xi, p));
+            x = x * w % p;
+            xi = xi * wi % p;
+        }
+        // scale = 2^32 * (2 Y K)^{-1} mod p
+        const uint64_t two32 = (1ull << 32) % p;
+        const uint64_t denom = (2ull * (uint64_t)(Y % p) % p) * (uint64_t)K % p;
+        const uint32_t scale = (uint32_t)(two32 * invmod((uint32_t)denom, p) % p);
+        x = 1;
+        xi = 1;
+        for (int e = 0; e < 2 * K; ++e) {
+            blk[L.tx_f + e] = make_uint2((uint32_t)x, shoup_q((uint32_t)x, p));
+            blk[L.tx_i + e] = make_uint2((uint32_t)xi, shoup_q((uint32_t)xi, p));
+            if (e < K) {
+                uint32_t u = (uint32_t)((uint64_t)scale * xi % p);
+                blk[L.untw + e] = make_uint2(u, shoup_q(u, p));
+            }
+            x = x * th % p;
+            xi = xi * thi % p;
+        }
+        PrimeConst &pc = kp.pc[t];
+        pc.p = p;
+        pc.p2 = 2 * p;
+        uint32_t inv = p;  // Newton iteration for p^{-1} mod 2^32
+        for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
+        pc.mont = 0u - inv;
+        pc.one_s = shoup_q(1, p);
+        pc.c32 = (uint32_t)two32;
+        pc.c32_s = shoup_q(pc.c32, p);
+        pc.scale = scale;
+        pc.scale_s = shoup_q(scale, p);
+    }
+    for (int t = 0; t < kp.r; ++t)
+        for (int s = 0; s < t; ++s) {
+            uint32_t pt = kp.pc[t].p;
+            uint32_t g = invmod(kp.pc[s].p % pt, pt);
+            kp.ginv[t][s] = g;
+            kp.ginv_s[t][s] = shoup_q(g, pt);
+        }
+    // m = prod p_t in r words (each p < 2^30 so r words suffice)
+    uint32_t mw[RMAX + 1] = {1};
+    for (int t = 0; t < kp.r; ++t) {
+        uint64_t carry = 0;
+        for (int i = 0; i <= RMAX; ++i) {
+            uint64_t v = (uint64_t)mw[i] * kp.pc[t].p + carry;
+            mw[i] = (uint32_t)v;
+            carry = v >> 32;
+        }
+    }
+    for (int i = 0; i < RMAX; ++i) kp.m_words[i] = i < kp.r ? mw[i] : 0;
+}
+
+}  // namespace ipm
+
+extern "C" ipm_status ipm_choose(const ipm_shape *shape, const ipm_params *params,
+                                 ipm_plan_info *out) {
+    if (!shape || !out) return IPM_ERR_ARG;
+    ipm::ShapePlan sp;
+    ipm_status st = ipm::choose_plan(*shape, params, sp);
+    if (st != IPM_OK) return st;
+    *out = sp.info;
+    return IPM_OK;
+}

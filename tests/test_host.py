@@ -1,0 +1,123 @@
+"""Host-side tests (no GPU): the library loads, exports every symbol the
+header declares, and the planner (DetermineBase / RecoveryPrime, §2, §2.1,
+§4) obeys the paper's conditions."""
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1612_05778_gb300 as ipm
+from paper_1612_05778_gb300 import build as ipm_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ipm_build.build()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ipm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ipm_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    syms = declared_symbols()
+    for s in ("ipm_plan", "ipm_mul", "ipm_mul_batched", "ipm_destroy", "ipm_choose", "ipm_mul_host"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    out = subprocess.check_output(["nm", "-D", "--defined-only", ipm.LIB_PATH]).decode()
+    exported = set(re.findall(r"\sT\s+(\w+)", out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_without_gpu():
+    lib = ipm.load_library()
+    assert lib.ipm_strerror(0) == b"ok"
+    assert lib.ipm_strerror(2).startswith(b"input coefficient")
+
+
+SHAPES = [(1, 1, 1, 1), (1024, 1024, 255, 255), (32768, 32768, 4096, 4096), (8192, 16, 4096, 32),
+          (262144, 262144, 1024, 1024), (64, 64, 16384, 16384), (3, 700, 33, 7000), (100, 100, 31, 32)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_planner_invariants(shape):
+    na, nb, ba, bb = shape
+    I = ipm.choose(*shape)
+    K, M, N, r = I["K"], I["M"], I["N"], I["r"]
+    nc = na + nb - 1
+    # N = K M with K, M > 1, K a power of two, N >= bits + 1 (two's complement, Eq. definingN)
+    assert N == K * M and K >= 2 and M >= 2 and K & (K - 1) == 0
+    assert N >= max(ba, bb) + 1
+    # y length: power of two >= na + nb - 1 (acyclic product in y)
+    Y = I["Y"]
+    assert Y & (Y - 1) == 0 and Y >= nc and Y < 2 * max(nc, 1) + 1
+    assert I["Y1"] * I["Y2"] == Y
+    # every prime has roots of unity of order Y and 2K (Eq. HavingAppropriatePrimitiveRootsOfUnity)
+    ps = I["primes"]
+    assert len(ps) == r and ps == sorted(ps, reverse=True) and len(set(ps)) == r
+    for p in ps:
+        assert (1 << 29) < p < (1 << 30)
+        assert (p - 1) % max(Y, 2 * K) == 0
+    # m = prod p > 4H with H = min(na,nb) * K * 2^(2M-2) (the m > 4H of §1)
+    m = math.prod(ps)
+    H = min(na, nb) * K * (1 << (2 * M - 2))
+    assert m > 4 * H
+    # output stride: |c_k| < min(na,nb) 2^(ba+bb) fits in lc limbs
+    assert (1 << (32 * I["lc"])) >= min(na, nb) * (1 << (ba + bb))
+
+
+def test_planner_primes_are_prime():
+    sympy = pytest.importorskip("sympy")
+    for p in ipm.choose(262144, 262144, 1024, 1024)["primes"] + ipm.choose(64, 64, 16384, 16384)["primes"]:
+        assert sympy.isprime(p)
+
+
+def test_planner_picks_fewest_primes_for_its_split():
+    # r is minimal: dropping one prime breaks m > 4H
+    for shape in SHAPES:
+        I = ipm.choose(*shape)
+        if I["r"] == 1:
+            continue
+        m = math.prod(I["primes"][:-1])
+        H = min(shape[0], shape[1]) * I["K"] * (1 << (2 * I["M"] - 2))
+        assert m <= 4 * H
+
+
+@pytest.mark.parametrize("kw", [dict(K=3), dict(K=1), dict(M=1), dict(M=70), dict(r=7),
+                                dict(K=8, M=4), dict(r=1, K=8, M=32), dict(y2=3), dict(s=3)])
+def test_planner_rejects_invalid_overrides(kw):
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(1024, 1024, 255, 255, **kw)
+
+
+@pytest.mark.parametrize("shape", [(0, 5, 8, 8), (5, 5, 0, 8), (5, 5, 8, 70000)])
+def test_planner_rejects_bad_shapes(shape):
+    with pytest.raises(ipm.IpmError) as e:
+        ipm.choose(*shape)
+    assert e.value.status == 1
+
+
+def test_planner_accepts_valid_overrides():
+    base = ipm.choose(1024, 1024, 255, 255)
+    for kw in (dict(K=16), dict(K=8, M=40), dict(r=4), dict(y2=8), dict(s=2), dict(K=32, y2=1)):
+        I = ipm.choose(1024, 1024, 255, 255, **kw)
+        for k, v in kw.items():
+            key = {"y2": "Y2", "s": "S"}.get(k, k)
+            assert I[key] == v
+        assert I["lc"] == base["lc"] and I["nc"] == base["nc"]
+
+
+def test_unsupported_beyond_prime_order():
+    # Y would be 2^22 > 2^21, the 2-adic order of every prime
+    with pytest.raises(ipm.IpmError) as e:
+        ipm.choose(1 << 21, 1 << 21, 64, 64)
+    assert e.value.status == 6
