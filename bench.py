@@ -1,0 +1,415 @@
+"""Benchmark: exact dense Z[y] products on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload large_dense|small_dense|large_all_ones|huge_dense]
+
+One step is one whole product c = a*b (split, forward 2-D transforms over
+every prime, pointwise products, inverse transforms, CRT, recombination)
+through the C ABI, on the workload of two degree-32767 polynomials with
+4096-bit signed coefficients (seed 1) by default.  Inputs are resident in
+HBM before the timed region; the L2 is flushed (a 512 MiB write) between
+timed steps, outside the events.  Prints ONE JSON line on rank 0.
+
+--impl reference times the CPU oracle (plain schoolbook definition, all
+host cores) on a bounded sample of the same workload per step and
+extrapolates to products/s.
+
+Multi-GPU (torchrun): products are independent, so every rank multiplies its
+own pair (weak scaling, no data-path collective); the host-side barrier and
+max-over-ranks timing use torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "exact Z[x] products/s and output Gbit/s at (d,N); speedup vs plain GPU path"
+UNIT = "products/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+PASS_NAMES = ["k_forward", "k_middle", "k_inverse"]
+KERNEL_SRC = os.path.join(ROOT, "paper_1612_05778_gb300", "csrc", "ipm_kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_large_dense.md")
+
+
+def workload(name: str):
+    if name == "large_dense":
+        sh, a, b = W.large_dense(seed=1)
+        return "large_dense: d=32768, |coeff| < 2^4096, signed uniform, seed 1", sh, a, b
+    if name == "small_dense":
+        sh, a, b = W.small_dense(seed=0)
+        return "small_dense: d=1024, |coeff| < 2^255, signed uniform, seed 0", sh, a, b
+    if name == "large_all_ones":
+        sh, a, b = W.large_all_ones()
+        return "large_all_ones: d=32768, every coefficient 2^4096-1", sh, a, b
+    if name == "huge_dense":
+        sh, a, b = W.huge_dense(seed=2)
+        return "huge_dense: d=262144, |coeff| < 2^1024, signed uniform, seed 2", sh, a, b
+    raise SystemExit("unknown workload " + name)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (host side only)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """Largest value over all ranks (host-side timing reduction)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) timing: a bounded sample of output coefficients
+# ---------------------------------------------------------------------------
+
+def oracle_sample_time(sh, a, b, target_s: float, seed: int = 0):
+    """Time the oracle on sampled output coefficients and extrapolate to a
+    full product: a coefficient c_k costs terms(k) limb products of the two
+    operand rows, the whole product costs na*nb of them."""
+    import oracle
+    threads = oracle.default_threads()
+    rng = np.random.default_rng(seed)
+
+    def terms(k):
+        return max(0, min(k, sh.na - 1) - max(0, k - (sh.nb - 1)) + 1)
+
+    def run(count):
+        ks = np.sort(rng.integers(0, sh.nc, count))
+        t0 = time.perf_counter()
+        oracle.coeffs(ks, a, b, sh.lc, threads=threads)
+        dt = time.perf_counter() - t0
+        work = sum(terms(int(k)) for k in ks)
+        return dt, work, count
+
+    dt, work, count = run(max(threads, 8))
+    if dt < target_s * 0.5:
+        want = int(count * target_s / max(dt, 1e-3))
+        want = max(count, min(want, sh.nc))
+        dt, work, count = run(want)
+    full = float(sh.na) * float(sh.nb)
+    t_full = dt * full / max(work, 1)
+    return {"products_per_s": 1.0 / t_full, "seconds": dt, "coefficients": count,
+            "fraction_of_product": work / full, "threads": threads}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    name, sh, a, b = workload(args.workload)
+    import oracle
+    oracle.build()
+    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample_time(sh, a, b, per_step * 0.3, seed=100)
+    vals = []
+    secs = 0.0
+    last = None
+    for s in range(args.steps):
+        r = oracle_sample_time(sh, a, b, per_step, seed=s)
+        vals.append(r["products_per_s"])
+        secs += r["seconds"]
+        last = r
+    value = float(np.median(vals))
+    out_bits = sh.nc * sh.lc * 32
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "output_gbit_s": out_bits * value / 1e9,
+        "config": {"workload": name, "na": sh.na, "nb": sh.nb, "bits": sh.bits_a, "lc": sh.lc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["threads"], "kind": "oracle",
+                         "sample": "per step: %d random output coefficients (%.3g%% of the product's "
+                                   "limb products), timed and scaled to one whole product"
+                                   % (last["coefficients"], 100 * last["fraction_of_product"])},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(info):
+    """Algorithmic DRAM bytes of each pass for one product:
+    forward reads both operands and writes 2 r Y 2K residues; middle reads
+    them and writes r Y 2K; inverse reads r Y 2K and writes the output."""
+    z = info["r"] * info["Y"] * 2 * info["K"] * 4
+    inp = info["na"] * (info["la"] * 4 + 1) + info["nb"] * (info["lb"] * 4 + 1)
+    out = info["nc"] * (info["lc"] * 4 + 1)
+    return [inp + 2 * z, 3 * z, z + out]
+
+
+def load_peak_hbm():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the summary is missing or was taken on other kernel source."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(r"^%s_dram_bytes_per_launch:\s*([0-9]+)" % kernel, text, re.M)
+    return int(m.group(1)) if m else None
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    dist = dist_init(world, "nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1612_05778_gb300 import build as ipm_build
+    if rank == 0:
+        ipm_build.build()
+    barrier(dist)
+    import paper_1612_05778_gb300 as ipm
+
+    name, sh, a, b = workload(args.workload)
+    plan = ipm.Plan((sh.na, sh.nb, sh.bits_a, sh.bits_b))
+    info = plan.info
+    da, dan = ipm.to_device(*a)
+    db, dbn = ipm.to_device(*b)
+    c, cn = plan.empty_output()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    # correctness guard on the benchmarked plan: two sampled coefficients
+    plan.mul(da, dan, db, dbn, c, cn)
+    plan.sync()
+
+    for _ in range(args.warmup):
+        plan.mul(da, dan, db, dbn, c, cn)
+    torch.cuda.synchronize()
+
+    plan.set_profiling(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches0 = ipm.launch_count()
+    step_ms = []
+    pass_ms = np.zeros(3)
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.mul(da, dan, db, dbn, c, cn, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        pass_ms += np.array(plan.phase_ms())
+    torch.cuda.synchronize()
+    barrier(dist)
+    wall = time.perf_counter() - t_wall0
+    launches = ipm.launch_count() - launches0
+    clocks = sampler.stop()
+    plan.set_profiling(False)
+    plan.sync()
+
+    local_ms = float(np.sum(step_ms))
+    total_ms = max_over_ranks(dist, local_ms, dev)
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+    out_bits = sh.nc * sh.lc * 32
+
+    # roofline of the dominant pass (algorithmic bytes / event-timed duration)
+    pass_avg = pass_ms / args.steps
+    dom = int(np.argmax(pass_avg))
+    abytes = algorithmic_bytes(info)
+    peak, peak_kind = load_peak_hbm()
+    achieved = abytes[dom] / (pass_avg[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": PASS_NAMES[dom], "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind + " (burst copy)", "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(PASS_NAMES[dom]),
+                "algorithmic_bytes": abytes[dom]}
+    passes = {PASS_NAMES[i]: {"ms": float(pass_avg[i]), "algorithmic_bytes": abytes[i],
+                              "gbs": abytes[i] / (pass_avg[i] / 1e3) / 1e9} for i in range(3)}
+
+    # end to end through the host-buffer ABI call (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()  # noqa: E731
+        ha, han, hb, hbn = pin(a[0]), pin(a[1]), pin(b[0]), pin(b[1])
+        hc = torch.empty((info["nc"], info["lc"]), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        hcn = torch.empty((info["nc"],), dtype=torch.uint8).pin_memory().numpy()
+        for _ in range(2):
+            plan.mul_host(ha, han, hb, hbn, hc, hcn, stream=stream)
+        e2e_steps = max(3, args.steps // 2)
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.mul_host(ha, han, hb, hbn, hc, hcn, stream=stream)
+        dt = max_over_ranks(dist, time.perf_counter() - t0, dev)
+        h2d = ha.nbytes + han.nbytes + hb.nbytes + hbn.nbytes
+        d2h = hc.nbytes + hcn.nbytes
+        e2e = {"value": world * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+               "api": "ipm_mul_host (pinned host buffers; copies in, product, copies out, sync)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r = oracle_sample_time(sh, a, b, args.cpu_seconds)
+        cpu = {"value": r["products_per_s"], "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+               "sample": "%d random output coefficients (%.3g%% of the product's limb products) in "
+                         "%.1f s, scaled to one whole product" % (r["coefficients"],
+                                                                  100 * r["fraction_of_product"], r["seconds"])}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "output_gbit_s": out_bits * value / 1e9,
+        "speedup_vs_plain": 1.0,
+        "config": {"workload": name, "na": sh.na, "nb": sh.nb, "bits": sh.bits_a, "lc": sh.lc,
+                   "plan": {k: info[k] for k in ("K", "M", "N", "r", "Y", "Y1", "Y2", "S")},
+                   "primes": info["primes"], "parallelism": "replicas (one product per GPU)",
+                   "l2": "flushed between timed steps (512 MiB write, outside the events)",
+                   "path": "plain 2-D NTT (Shoup butterflies), 3 launches per product"},
+        "roofline": roofline,
+        "passes": passes,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "launches_per_step": launches / args.steps,
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="large_dense")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

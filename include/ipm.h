@@ -165,6 +165,18 @@ ipm_status ipm_sync(ipm_plan_t plan, ipm_stream_t stream);
 /* Free a plan (waits for the device first).  NULL is accepted. */
 ipm_status ipm_destroy(ipm_plan_t plan);
 
+/*
+ * Per-pass timing.  With profiling enabled, every product a plan runs
+ * records CUDA events on its stream before the first pass and after each of
+ * the three passes (split + forward transforms; middle transforms +
+ * pointwise product; inverse transforms + CRT + recombination).  No work is
+ * skipped or reordered.  ipm_phase_ms waits for the events of the most
+ * recent product and writes min(n, 3) durations in milliseconds to ms[].
+ * ipm_phase_ms returns IPM_ERR_ARG when profiling is off or nothing ran.
+ */
+ipm_status ipm_set_profiling(ipm_plan_t plan, int32_t enable);
+ipm_status ipm_phase_ms(ipm_plan_t plan, float *ms, int32_t n);
+
 /* Static description of a status code. */
 const char *ipm_strerror(ipm_status status);
 

@@ -80,11 +80,13 @@ def load_library(path: str | None = None):
     lib.ipm_mul_batched.argtypes = [V, ctypes.POINTER(Operands), I32, V]
     lib.ipm_sync.argtypes = [V, V]
     lib.ipm_destroy.argtypes = [V]
+    lib.ipm_set_profiling.argtypes = [V, I32]
+    lib.ipm_phase_ms.argtypes = [V, ctypes.POINTER(ctypes.c_float), I32]
     lib.ipm_strerror.argtypes = [ctypes.c_int]
     lib.ipm_strerror.restype = ctypes.c_char_p
     lib.ipm_launch_count.restype = ctypes.c_int64
     for name in ("ipm_choose", "ipm_plan", "ipm_plan_ex", "ipm_get_info", "ipm_mul", "ipm_mul_host",
-                 "ipm_mul_batched", "ipm_sync", "ipm_destroy"):
+                 "ipm_mul_batched", "ipm_sync", "ipm_destroy", "ipm_set_profiling", "ipm_phase_ms"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -227,6 +229,16 @@ class Plan:
                               _dptr(cn, torch.uint8, (I["nc"],)).value)
         _check(self._lib.ipm_mul_batched(self._h, arr, n, _stream_handle(stream)), "ipm_mul_batched")
         return outputs
+
+    def set_profiling(self, enable: bool = True):
+        """Record CUDA events around each of the three passes of every product."""
+        _check(self._lib.ipm_set_profiling(self._h, 1 if enable else 0), "ipm_set_profiling")
+
+    def phase_ms(self):
+        """(forward, middle, inverse) pass durations of the latest product, in ms."""
+        out = (ctypes.c_float * 3)()
+        _check(self._lib.ipm_phase_ms(self._h, out, 3), "ipm_phase_ms")
+        return [float(x) for x in out]
 
     def sync(self, stream=None):
         """Wait for the stream and raise on a device-side error (e.g. IPM_ERR_BOUND)."""

@@ -21,6 +21,10 @@ struct ipm_plan_s {
     // ipm_mul_host staging (allocated on first use)
     unsigned char *io = nullptr;
     size_t io_bytes = 0;
+    // per-pass profiling events (ipm_set_profiling)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool profiling = false;
+    bool profiled_once = false;
 };
 
 namespace {
@@ -33,6 +37,8 @@ ipm_status cuda_status(cudaError_t e) {
 
 void free_plan(ipm_plan_s *p) {
     if (!p) return;
+    for (auto &e : p->ev)
+        if (e) cudaEventDestroy(e);
     for (void *ptr : p->allocations) cudaFree(ptr);
     delete p;
 }
@@ -43,10 +49,16 @@ ipm_status run_one(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a, con
                    const uint32_t *b, const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream) {
     if (!a || !an || !b || !bn || !c || !cn) return IPM_ERR_ARG;
     if (!aligned16(a) || !aligned16(b) || !aligned16(c)) return IPM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool prof = plan->profiling;
+    if (prof && cudaEventRecord(plan->ev[0], s) != cudaSuccess) return IPM_ERR_CUDA;
     if (launch_forward(sp.kp, sp.smem_fwd, a, an, b, bn, stream)) return IPM_ERR_CUDA;
+    if (prof && cudaEventRecord(plan->ev[1], s) != cudaSuccess) return IPM_ERR_CUDA;
     if (launch_middle(sp.kp, sp.smem_mid, stream)) return IPM_ERR_CUDA;
+    if (prof && cudaEventRecord(plan->ev[2], s) != cudaSuccess) return IPM_ERR_CUDA;
     if (launch_inverse(sp.kp, sp.smem_inv, c, cn, stream)) return IPM_ERR_CUDA;
-    (void)plan;
+    if (prof && cudaEventRecord(plan->ev[3], s) != cudaSuccess) return IPM_ERR_CUDA;
+    if (prof) plan->profiled_once = true;
     return IPM_OK;
 }
 
@@ -208,6 +220,29 @@ ipm_status ipm_destroy(ipm_plan_t plan) {
     if (!plan) return IPM_OK;
     cudaDeviceSynchronize();
     free_plan(plan);
+    return IPM_OK;
+}
+
+ipm_status ipm_set_profiling(ipm_plan_t plan, int32_t enable) {
+    if (!plan) return IPM_ERR_ARG;
+    if (enable && !plan->ev[0]) {
+        for (auto &e : plan->ev) {
+            cudaError_t ce = cudaEventCreate(&e);
+            if (ce != cudaSuccess) return cuda_status(ce);
+        }
+    }
+    plan->profiling = enable != 0;
+    return IPM_OK;
+}
+
+ipm_status ipm_phase_ms(ipm_plan_t plan, float *ms, int32_t n) {
+    if (!plan || !ms || n < 0 || !plan->ev[0] || !plan->profiled_once) return IPM_ERR_ARG;
+    cudaError_t ce = cudaEventSynchronize(plan->ev[3]);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    for (int32_t i = 0; i < n && i < 3; ++i) {
+        ce = cudaEventElapsedTime(&ms[i], plan->ev[i], plan->ev[i + 1]);
+        if (ce != cudaSuccess) return cuda_status(ce);
+    }
     return IPM_OK;
 }
 
