@@ -159,6 +159,38 @@ typedef struct {
 ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n,
                            ipm_stream_t stream);
 
+/*
+ * A product that allocates nothing (no counterpart in the paper; this is an
+ * interface convenience).  For callers that cannot allocate device memory
+ * while they run: code recording a CUDA graph by stream capture (cudaMalloc
+ * is not permitted during capture), real-time services that forbid
+ * allocator calls (cudaMalloc may synchronise the device), and plugins
+ * whose host application owns all memory and hands over only the operand
+ * buffers.
+ *
+ * Same arguments and layouts as ipm_mul (device pointers), but no plan: the
+ * shape is given directly and the planner's default choices are used.  The
+ * product's scratch -- error word, twiddle tables and transform workspace --
+ * lives in one static device array of IPM_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading this library holds until the process exits; products whose
+ * scratch does not fit return IPM_ERR_UNSUPPORTED (for example two
+ * degree-1023 polynomials with 255-bit coefficients need 0.85 MiB, two of
+ * degree 2047 with 2048-bit coefficients 12.2 MiB, two of degree 4095 with
+ * 4096-bit coefficients 48.4 MiB, which is rejected).
+ *
+ * The first call on a device looks up the array's device address and sets
+ * kernel limits: make it before any stream capture.  All calls share the
+ * array, which keeps the previous call's contents (the error word is
+ * cleared and the tables rewritten each call), so calls that overlap on the
+ * GPU -- from several streams or host threads -- race: issue them one after
+ * another.  The call waits for `stream` and returns the product's status
+ * (IPM_ERR_BOUND for an input above its bit bound).
+ */
+#define IPM_NOALLOC_SCRATCH_BYTES (32u << 20)
+ipm_status ipm_mul_noalloc(const ipm_shape *shape, const uint32_t *a, const uint8_t *a_neg,
+                           const uint32_t *b, const uint8_t *b_neg,
+                           uint32_t *c, uint8_t *c_neg, ipm_stream_t stream);
+
 /* Wait for `stream`, then return and clear the plan's device error word. */
 ipm_status ipm_sync(ipm_plan_t plan, ipm_stream_t stream);
 

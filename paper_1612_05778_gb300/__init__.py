@@ -82,11 +82,13 @@ def load_library(path: str | None = None):
     lib.ipm_destroy.argtypes = [V]
     lib.ipm_set_profiling.argtypes = [V, I32]
     lib.ipm_phase_ms.argtypes = [V, ctypes.POINTER(ctypes.c_float), I32]
+    lib.ipm_mul_noalloc.argtypes = [ctypes.POINTER(Shape), V, V, V, V, V, V, V]
     lib.ipm_strerror.argtypes = [ctypes.c_int]
     lib.ipm_strerror.restype = ctypes.c_char_p
     lib.ipm_launch_count.restype = ctypes.c_int64
     for name in ("ipm_choose", "ipm_plan", "ipm_plan_ex", "ipm_get_info", "ipm_mul", "ipm_mul_host",
-                 "ipm_mul_batched", "ipm_sync", "ipm_destroy", "ipm_set_profiling", "ipm_phase_ms"):
+                 "ipm_mul_batched", "ipm_sync", "ipm_destroy", "ipm_set_profiling", "ipm_phase_ms",
+                 "ipm_mul_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -245,6 +247,32 @@ class Plan:
         _check(self._lib.ipm_sync(self._h, _stream_handle(stream)), "ipm_sync")
 
 
+# Size of the static device scratch of mul_noalloc (IPM_NOALLOC_SCRATCH_BYTES).
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def mul_noalloc(na: int, nb: int, bits_a: int, bits_b: int, a, a_neg, b, b_neg, c, c_neg,
+                stream=None):
+    """c = a*b without allocating anything: for callers that may not allocate
+    device memory while they run (stream capture, allocator-free services,
+    plugins whose host owns all memory).  All tensors are caller-owned CUDA
+    tensors (limbs int32 (n, L), signs uint8 (n,)); scratch comes from one
+    static device array shared by every call, so calls must not overlap on
+    the GPU.  Waits for the stream; raises IpmError on failure
+    (IPM_ERR_UNSUPPORTED when the product's scratch exceeds the array)."""
+    import torch
+    lib = load_library()
+    la, lb = (bits_a + 31) // 32, (bits_b + 31) // 32
+    args = [_dptr(a, torch.int32, (na, la)), _dptr(a_neg, torch.uint8, (na,)),
+            _dptr(b, torch.int32, (nb, lb)), _dptr(b_neg, torch.uint8, (nb,)),
+            _dptr(c, torch.int32), _dptr(c_neg, torch.uint8, (na + nb - 1,))]
+    if c.dim() != 2 or c.shape[0] != na + nb - 1:
+        raise ValueError("c must have na + nb - 1 rows")
+    _check(lib.ipm_mul_noalloc(ctypes.byref(Shape(na - 1, nb - 1, bits_a, bits_b)), *args,
+                               _stream_handle(stream)), "ipm_mul_noalloc")
+    return c, c_neg
+
+
 def to_device(limbs: np.ndarray, neg: np.ndarray):
     """numpy (uint32 limbs, uint8 signs) -> CUDA tensors (int32 view, uint8)."""
     import torch
@@ -259,4 +287,4 @@ def to_host(c, c_neg):
 
 
 __all__ = ["Plan", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
-           "IPM_SYNC", "LIB_PATH"]
+           "IPM_SYNC", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES"]
