@@ -27,9 +27,9 @@ constexpr int ERRBIT_BOUND = 1;      // an input coefficient >= 2^bits
 constexpr int ERRBIT_INTERNAL = 2;   // recombination top limb not a sign word
 
 // Bytes of per-warp recombination staging in the inverse pass: lc+1
-// limbs (u32) plus lc+1 carry bytes, rounded up to 16.
+// limbs (u32), rounded up to 16.
 __host__ __device__ inline size_t stage_bytes_per_warp(int lc) {
-    return (((size_t)lc + 1) * 5 + 15) & ~(size_t)15;
+    return (((size_t)lc + 1) * 4 + 15) & ~(size_t)15;
 }
 
 // Per-prime constants.  Twiddle tables hold (w, floor(w * 2^32 / p)) pairs

@@ -23,6 +23,7 @@
 
 #include "ipm_internal.h"
 #include "modarith.cuh"
+#include "ntt_stages.cuh"
 
 namespace ipm {
 
@@ -35,15 +36,14 @@ int64_t launches_so_far() { return g_launches.load(); }
 
 // Limb l of the N-bit two's complement of a sign-magnitude coefficient
 // (row: L magnitude limbs; f: index of its lowest non-zero limb).
-__device__ __forceinline__ uint32_t twos_limb(const uint32_t *__restrict__ row, int L, bool neg,
-                                              int f, int l) {
-    const uint32_t v = l < L ? __ldg(row + l) : 0u;
+__device__ __forceinline__ uint32_t twos_limb(const uint32_t *row, int L, bool neg, int f, int l) {
+    const uint32_t v = l < L ? row[l] : 0u;
     if (!neg) return v;
     if (l < f) return 0u;
     return l == f ? 0u - v : ~v;
 }
 
-__global__ void __launch_bounds__(THREADS_FWD)
+__global__ void __launch_bounds__(THREADS_FWD, 3)
 k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a,
           const uint8_t *__restrict__ an, const uint32_t *__restrict__ b,
           const uint8_t *__restrict__ bn) {
@@ -58,8 +58,9 @@ k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a,
     const int K = P.K, logK = P.logK, M = P.M;
     const int Y2 = (int)P.Y2;
     const int twoK = 2 * K;
+    const int pitch = twoK + 1;  // odd row pitch: column walks hit distinct banks
     int64_t *dig = reinterpret_cast<int64_t *>(smem);            // [Y2][K]
-    uint32_t *tile = reinterpret_cast<uint32_t *>(dig + (size_t)Y2 * K);  // [Y2][2K]
+    uint32_t *tile = reinterpret_cast<uint32_t *>(dig + (size_t)Y2 * K);  // [Y2][pitch]
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint64_t mmask = (1ull << M) - 1;
@@ -72,22 +73,33 @@ k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a,
     //    generate g_j = [u_j >= 2^(M-1)] and propagate q_j = [u_j = 2^(M-1)-1]
     //    the carries into every digit are (g + (g|q)) xor q (carry-lookahead
     //    by integer addition), 32 digits per ballot word.
+    // rows i2 < nr hold coefficients (i = i1 + Y1*i2 < nX); the rest are the
+    // zero padding of the acyclic y-convolution
+    const int64_t Y1 = P.Y1;
+    const int nr = i1 < nX ? (int)min((int64_t)Y2, (nX - i1 + Y1 - 1) / Y1) : 0;
+    // 0. stage the magnitude limbs of the non-zero rows (L <= 2K < pitch, so
+    //    row i2 fits at tile + i2 * pitch), all loads in flight at once
+    for (int e = threadIdx.x; e < nr * L; e += blockDim.x) {
+        const int i2 = e / L, l = e - i2 * L;
+        tile[(size_t)i2 * pitch + l] = __ldg(X + (size_t)(i1 + Y1 * i2) * L + l);
+    }
+    __syncthreads();
     for (int i2 = warp; i2 < Y2; i2 += nw) {
-        const int64_t i = i1 + P.Y1 * (int64_t)i2;
+        const int64_t i = i1 + Y1 * (int64_t)i2;
         int64_t *drow = dig + (size_t)i2 * K;
-        if (i >= nX) {
+        if (i2 >= nr) {
             for (int j = lane; j < K; j += 32) drow[j] = 0;
             continue;
         }
-        const uint32_t *row = X + (size_t)i * L;
+        const uint32_t *row = tile + (size_t)i2 * pitch;
         int f = L;
         for (int c0 = 0; c0 < L; c0 += 32) {
             const int l = c0 + lane;
-            const uint32_t v = l < L ? __ldg(row + l) : 0u;
+            const uint32_t v = l < L ? row[l] : 0u;
             const unsigned m = __ballot_sync(0xffffffffu, v != 0u);
             if (m && f == L) f = c0 + __ffs(m) - 1;
         }
-        if (lane == 0 && (bits & 31u) && (__ldg(row + L - 1) >> (bits & 31u)))
+        if (lane == 0 && (bits & 31u) && (row[L - 1] >> (bits & 31u)))
             atomicOr(P.err, ERRBIT_BOUND);
         const bool neg = Xn[i] != 0 && f < L;
         unsigned carry_in = 0;
@@ -124,35 +136,42 @@ k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a,
     }
     __syncthreads();
 
-    const int64_t Y1 = P.Y1;
     for (int t = 0; t < P.r; ++t) {
         const PrimeConst &pc = P.pc[t];
         const uint32_t p = pc.p, p2 = pc.p2;
         const uint2 one = make_uint2(1u, pc.one_s), c32 = make_uint2(pc.c32, pc.c32_s);
         // 2. residues (cyclic half) and twisted residues theta^j a_ij (negacyclic half)
-        for (int e = threadIdx.x; e < Y2 * K; e += blockDim.x) {
+        for (int e = threadIdx.x; e < nr * K; e += blockDim.x) {
             const int i2 = e >> logK, j = e & (K - 1);
             const int64_t d = dig[e];
             const uint64_t ad = d < 0 ? (uint64_t)(-d) : (uint64_t)d;
             uint32_t r = shoup((uint32_t)(ad >> 32), c32, p) + shoup((uint32_t)ad, one, p);
             r = red(red(r, p2), p);
             if (d < 0 && r) r = p - r;
-            uint32_t *trow = tile + (size_t)i2 * twoK;
+            uint32_t *trow = tile + (size_t)i2 * pitch;
             trow[j] = r;
-            trow[K + j] = shoup(r, pc.tx_f[j], p);
+            trow[K + j] = shoup(r, __ldg(pc.tx_f + j), p);
+        }
+        for (int e = threadIdx.x; e < (Y2 - nr) * twoK; e += blockDim.x) {
+            const int i2 = nr + (e >> (logK + 1)), col = e & (twoK - 1);
+            tile[(size_t)i2 * pitch + col] = 0u;
         }
         __syncthreads();
-        // 3. x-DFTs of length K on both halves of every row (omega_K = theta^2)
-        dif_rows(tile, 2 * Y2, K, logK, pc.tx_f, logK + 1, p, p2);
+        // 3. x-DFTs of length K on both halves of the non-zero rows (omega_K = theta^2)
+        if (nr > 0) {
+            const TileMap xm{tile, 2 * nr, nr, pitch, K, 1};
+            ntt_forward(xm, logK, pc.tx_f, logK + 1, p, p2);
+        }
         // 4. y step A: length-Y2 DFT down every column
-        dif_cols(tile, logK + 1, twoK, P.logY2, pc.ty_f, P.logY, p, p2);
+        const TileMap ym{tile, twoK, twoK, 1, 0, pitch};
+        ntt_forward(ym, P.logY2, pc.ty_f, P.logY, p, p2);
         // 5. step B twiddle, full reduction, store rows (k2, i1)
         uint32_t *Zt = P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK;
         for (int e = threadIdx.x; e < Y2 * twoK; e += blockDim.x) {
             const int pos = e >> (logK + 1), col = e & (twoK - 1);
             const uint32_t k2 = bitrev((uint32_t)pos, P.logY2);
-            const uint2 w = pc.ty_f[(size_t)i1 * k2];
-            const uint32_t v = red(shoup(tile[e], w, p), p);
+            const uint2 w = __ldg(pc.ty_f + (size_t)i1 * k2);
+            const uint32_t v = red(shoup(tile[(size_t)pos * pitch + col], w, p), p);
             Zt[((size_t)pos * Y1 + i1) * twoK + col] = v;
         }
         __syncthreads();
@@ -163,14 +182,15 @@ k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a,
 // Pass 2
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(THREADS_MID) k_middle(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant__ KParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int cs = blockIdx.x, pos = blockIdx.y, t = blockIdx.z;
     const int S = P.S, logS = P.logS;
+    const int pitch = S + 1;  // odd pitch for conflict-free strided gathers
     const int twoK = 2 * P.K;
     const int Y1 = (int)P.Y1;
-    uint32_t *A = reinterpret_cast<uint32_t *>(smem);  // [Y1][S]
-    uint32_t *B = A + (size_t)Y1 * S;                   // [Y1][S]
+    uint32_t *A = reinterpret_cast<uint32_t *>(smem);  // [Y1][pitch]
+    uint32_t *B = A + (size_t)Y1 * pitch + 16;          // [Y1][pitch], shifted 16 banks
     const PrimeConst &pc = P.pc[t];
     const uint32_t p = pc.p, p2 = pc.p2;
     uint32_t *ZA = P.Z + (size_t)(t * 2 + 0) * (size_t)P.Y * twoK;
@@ -179,21 +199,25 @@ __global__ void __launch_bounds__(THREADS_MID) k_middle(const __grid_constant__ 
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
         const int i1 = e >> logS, c = e & (S - 1);
         const size_t g = base + (size_t)i1 * twoK + c;
-        A[e] = ZA[g];
-        B[e] = ZB[g];
+        A[i1 * pitch + c] = ZA[g];
+        B[i1 * pitch + c] = ZB[g];
     }
     __syncthreads();
-    // y step C (omega_Y1 = omega_Y^Y2) on A and B
-    dif_cols(A, logS, S, P.logY1, pc.ty_f, P.logY, p, p2);
-    dif_cols(B, logS, S, P.logY1, pc.ty_f, P.logY, p, p2);
+    // y step C (omega_Y1 = omega_Y^Y2) on the S columns of A and of B
+    const TileMap both{A, 2 * S, S, 1, (int)(B - A), pitch};
+    ntt_forward(both, P.logY1, pc.ty_f, P.logY, p, p2);
     // pointwise product in Montgomery form: A*B*2^-32 (the 2^32 is put back
     // by the scale factor of the inverse pass)
-    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) A[e] = montmul(A[e], B[e], p, pc.mont);
+    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+        const int i = (e >> logS) * pitch + (e & (S - 1));
+        A[i] = montmul(A[i], B[i], p, pc.mont);
+    }
     __syncthreads();
-    dit_cols(A, logS, S, P.logY1, pc.ty_i, P.logY, p, p2);
+    const TileMap am{A, S, S, 1, 0, pitch};
+    ntt_inverse(am, P.logY1, pc.ty_i, P.logY, p, p2);
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
         const int i1 = e >> logS, c = e & (S - 1);
-        ZA[base + (size_t)i1 * twoK + c] = red(A[e], p);
+        ZA[base + (size_t)i1 * twoK + c] = red(A[i1 * pitch + c], p);
     }
 }
 
@@ -201,43 +225,114 @@ __global__ void __launch_bounds__(THREADS_MID) k_middle(const __grid_constant__ 
 // Pass 3
 // ---------------------------------------------------------------------------
 
-// Carry-in function of one limb: cin in {-1,0,1} -> carry out in {-1,0,1},
-// packed as three 2-bit fields (value + 1) at bits 0, 2, 4 for cin = -1, 0, 1.
-__device__ __forceinline__ int fn_apply(unsigned code, int c) {
-    return (int)((code >> (2 * (c + 1))) & 3u) - 1;
-}
-__device__ __forceinline__ unsigned fn_compose(unsigned outer, unsigned inner) {
-    unsigned r = 0;
-#pragma unroll
-    for (int c = -1; c <= 1; ++c) r |= (unsigned)(fn_apply(outer, fn_apply(inner, c)) + 1) << (2 * (c + 1));
-    return r;
-}
-constexpr unsigned FN_IDENTITY = 0u | (1u << 2) | (2u << 4);
-
-// Sum of the contributions to limb q of sum_j V_j 2^{Mj}, where V_j is an
-// r-word two's-complement value at V[w * wstride + j] (mod 2^(32(lc+1))).
-// V_j 2^sh is read as r unsigned words plus one signed top word.
-__device__ __forceinline__ int64_t limb_sum(const uint32_t *V, size_t wstride, int q, int M, int r,
-                                            int twoK) {
-    if (q < 0) return 0;
-    int jlo = q - r <= 0 ? 0 : (32 * (q - r) + M - 1) / M;
+// Contribution ranges of the recombination: limb q of sum_j V_j 2^{Mj}
+// receives pieces of V_j for jlo(q) <= j <= jhi(q) (V_j spans r words plus a
+// sign word above bit Mj).  Packed as jlo | count << 16.
+__device__ __forceinline__ uint32_t contrib_range(int q, int M, int r, int twoK) {
+    const int jlo = q - r <= 0 ? 0 : (32 * (q - r) + M - 1) / M;
     int jhi = (32 * q + 31) / M;
     if (jhi > twoK - 1) jhi = twoK - 1;
+    const int cnt = jhi >= jlo ? jhi - jlo + 1 : 0;
+    return (uint32_t)jlo | ((uint32_t)cnt << 16);
+}
+
+// Sum of the contributions to limb q of sum_j V_j 2^{Mj}, where V_j is an
+// r-word two's-complement value at V[w * plane + j] (mod 2^(32(lc+1))).
+// V_j 2^sh is read as r unsigned words plus one signed top word.
+__device__ __forceinline__ int64_t limb_sum(const uint32_t *V, size_t plane, int q, int M, int r,
+                                            uint32_t range) {
+    const int jlo = (int)(range & 0xffffu), cnt = (int)(range >> 16);
+    int e = M * jlo;
     int64_t acc = 0;
-    for (int j = jlo; j <= jhi; ++j) {
-        const int e = M * j;
+    for (int n = 0; n < cnt; ++n, e += M) {
+        const int j = jlo + n;
         const int k = q - (e >> 5), sh = e & 31;
-        if (k < 0 || k > r) continue;
         if (k < r) {
-            const uint32_t hi = V[(size_t)k * wstride + j];
-            const uint32_t lo = k > 0 ? V[(size_t)(k - 1) * wstride + j] : 0u;
+            const uint32_t hi = V[(size_t)k * plane + j];
+            const uint32_t lo = k > 0 ? V[(size_t)(k - 1) * plane + j] : 0u;
             acc += (int64_t)(sh ? __funnelshift_l(lo, hi, sh) : hi);
         } else {
-            const int32_t top = (int32_t)V[(size_t)(r - 1) * wstride + j];
-            acc += (int64_t)(sh ? (top >> (32 - sh)) : (top < 0 ? -1 : 0));
+            const int32_t top = (int32_t)V[(size_t)(r - 1) * plane + j];
+            acc += (int64_t)(sh ? (top >> (32 - sh)) : (top >> 31));
         }
     }
     return acc;
+}
+
+// Carries into each lane of a 32-limb chunk from per-lane generate and
+// propagate bits (disjoint) and the chunk's carry-in: carry-lookahead by
+// one 33-bit addition.  Returns the carry mask; *cio becomes the carry out.
+__device__ __forceinline__ unsigned lookahead(unsigned gen, unsigned prop, unsigned *cio) {
+    const uint64_t s = (uint64_t)gen + (uint64_t)(gen | prop) + *cio;
+    *cio = (unsigned)(s >> 32);
+    return (unsigned)s ^ prop;
+}
+
+// CRT over RR primes (Garner's mixed radix) for every (row < nro, column)
+// of the tile, centred lift to (-m/2, m/2), written back as an RR-word
+// two's-complement value (word w in plane w).
+template <int RR>
+__device__ __forceinline__ void crt_tile(const KParams &P, uint32_t *R, size_t plane, int pitch,
+                                         int nro, int logK) {
+    const int twoK = 2 << logK;
+    uint32_t pr[RR];
+    uint2 gi[RR][RR];
+#pragma unroll
+    for (int t = 0; t < RR; ++t) {
+        pr[t] = P.pc[t].p;
+#pragma unroll
+        for (int s = 0; s < t; ++s) gi[t][s] = make_uint2(P.ginv[t][s], P.ginv_s[t][s]);
+    }
+    for (int e2 = threadIdx.x; e2 < nro * twoK; e2 += blockDim.x) {
+        const int e = (e2 >> (logK + 1)) * pitch + (e2 & (twoK - 1));
+        uint32_t v[RR];
+#pragma unroll
+        for (int t = 0; t < RR; ++t) v[t] = R[(size_t)t * plane + e];
+#pragma unroll
+        for (int t = 1; t < RR; ++t) {
+            uint32_t y = v[t];
+#pragma unroll
+            for (int s = 0; s < t; ++s) {
+                const uint32_t vs = red(v[s], pr[t]);  // v_s < 2^30 < 2 p_t
+                y = red(shoup(y + pr[t] - vs, gi[t][s], pr[t]), pr[t]);
+            }
+            v[t] = y;
+        }
+        // X = v0 + p0 (v1 + p1 (v2 + ...))
+        uint32_t X[RR];
+#pragma unroll
+        for (int w = 0; w < RR; ++w) X[w] = 0;
+        X[0] = v[RR - 1];
+#pragma unroll
+        for (int t = RR - 2; t >= 0; --t) {
+            uint64_t carry = v[t];
+#pragma unroll
+            for (int w = 0; w < RR; ++w) {
+                const uint64_t z = (uint64_t)X[w] * pr[t] + carry;
+                X[w] = (uint32_t)z;
+                carry = z >> 32;
+            }
+        }
+        // 2X >= m  <=>  X > (m-1)/2 (m is odd)  ->  X - m
+        uint32_t borrow = 0;
+#pragma unroll
+        for (int w = 0; w < RR; ++w) {
+            const uint32_t x2 = (X[w] << 1) | (w ? (X[w - 1] >> 31) : 0u);
+            const uint64_t d = (uint64_t)x2 - P.m_words[w] - borrow;
+            borrow = (uint32_t)(d >> 63);
+        }
+        if (!borrow) {
+            uint32_t bb = 0;
+#pragma unroll
+            for (int w = 0; w < RR; ++w) {
+                const uint64_t d = (uint64_t)X[w] - P.m_words[w] - bb;
+                X[w] = (uint32_t)d;
+                bb = (uint32_t)(d >> 63);
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < RR; ++w) R[(size_t)w * plane + e] = X[w];
+    }
 }
 
 __global__ void __launch_bounds__(THREADS_INV)
@@ -247,12 +342,18 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
     const int K = P.K, logK = P.logK, twoK = 2 * K, r = P.r, M = P.M;
     const int Y2 = (int)P.Y2;
     const int64_t Y1 = P.Y1;
-    const size_t plane = (size_t)Y2 * twoK;
-    uint32_t *R = reinterpret_cast<uint32_t *>(smem);  // [r][Y2][2K]
+    const int pitch = twoK + 1;  // odd row pitch
+    const size_t plane = (size_t)Y2 * pitch;
+    uint32_t *R = reinterpret_cast<uint32_t *>(smem);  // [r][Y2][pitch]
     const int lc1 = P.lc + 1;
+    uint32_t *ranges = R + (size_t)r * plane;          // [lc1]
+    unsigned char *stage_base =
+        reinterpret_cast<unsigned char *>(ranges) + (((size_t)lc1 * 4 + 15) & ~(size_t)15);
     const size_t stage_bytes = stage_bytes_per_warp(P.lc);
-    unsigned char *stage_base = smem + (size_t)r * plane * 4;
+    for (int q = threadIdx.x; q < lc1; q += blockDim.x) ranges[q] = contrib_range(q, M, r, twoK);
 
+    // rows i2 < nro are output coefficients (i = i1 + Y1*i2 < nc)
+    const int nro = i1 < P.nc ? (int)min((int64_t)Y2, (P.nc - i1 + Y1 - 1) / Y1) : 0;
     for (int t = 0; t < r; ++t) {
         const PrimeConst &pc = P.pc[t];
         const uint32_t p = pc.p, p2 = pc.p2;
@@ -262,132 +363,91 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
             const int pos = e >> (logK + 1), col = e & (twoK - 1);
             const uint32_t k2 = bitrev((uint32_t)pos, P.logY2);
             const uint32_t v = Zt[((size_t)pos * Y1 + i1) * twoK + col];
-            Rt[e] = shoup(v, pc.ty_i[(size_t)i1 * k2], p);
+            Rt[(size_t)pos * pitch + col] = shoup(v, __ldg(pc.ty_i + (size_t)i1 * k2), p);
         }
         __syncthreads();
-        dit_cols(Rt, logK + 1, twoK, P.logY2, pc.ty_i, P.logY, p, p2);
-        dit_rows(Rt, 2 * Y2, K, logK, pc.tx_i, logK + 1, p, p2);
+        const TileMap ym{Rt, twoK, twoK, 1, 0, pitch};
+        ntt_inverse(ym, P.logY2, pc.ty_i, P.logY, p, p2);
+        if (nro > 0) {
+            const TileMap xm{Rt, 2 * nro, nro, pitch, K, 1};
+            ntt_inverse(xm, logK, pc.tx_i, logK + 1, p, p2);
+        }
         const uint2 sc = make_uint2(pc.scale, pc.scale_s);
-        for (int e = threadIdx.x; e < Y2 * K; e += blockDim.x) {
+        for (int e = threadIdx.x; e < nro * K; e += blockDim.x) {
             const int i2 = e >> logK, j = e & (K - 1);
-            uint32_t *row = Rt + (size_t)i2 * twoK;
+            uint32_t *row = Rt + (size_t)i2 * pitch;
             const uint32_t u = shoup(row[j], sc, p);
-            const uint32_t v = shoup(row[K + j], pc.untw[j], p);
+            const uint32_t v = shoup(row[K + j], __ldg(pc.untw + j), p);
             row[j] = red(red(u + v, p2), p);
             row[K + j] = red(red(u - v + p2, p2), p);
         }
         __syncthreads();
     }
 
-    // CRT (Garner's mixed radix), centred lift to (-m/2, m/2), r-word
-    // two's complement written back over the residues (word w in plane w).
-    for (int e = threadIdx.x; e < (int)plane; e += blockDim.x) {
-        uint32_t v[RMAX];
-        v[0] = R[e];
-        for (int t = 1; t < r; ++t) {
-            const uint32_t pt = P.pc[t].p;
-            uint32_t y = R[(size_t)t * plane + e];
-            for (int s = 0; s < t; ++s) {
-                const uint32_t vs = red(v[s], pt);  // v_s < 2^30 < 2 p_t
-                y = red(shoup(y + pt - vs, make_uint2(P.ginv[t][s], P.ginv_s[t][s]), pt), pt);
-            }
-            v[t] = y;
-        }
-        uint32_t X[RMAX];
-#pragma unroll
-        for (int w = 0; w < RMAX; ++w) X[w] = 0;
-        X[0] = v[r - 1];
-        for (int t = r - 2; t >= 0; --t) {
-            uint64_t carry = v[t];
-            const uint32_t pt = P.pc[t].p;
-            for (int w = 0; w < r; ++w) {
-                const uint64_t z = (uint64_t)X[w] * pt + carry;
-                X[w] = (uint32_t)z;
-                carry = z >> 32;
-            }
-        }
-        // 2X >= m  <=>  X > (m-1)/2 (m is odd)  ->  X - m
-        uint32_t borrow = 0;
-        for (int w = 0; w < r; ++w) {
-            const uint32_t x2 = (X[w] << 1) | (w ? (X[w - 1] >> 31) : 0u);
-            const uint64_t d = (uint64_t)x2 - P.m_words[w] - borrow;
-            borrow = (uint32_t)(d >> 63);
-        }
-        if (!borrow) {
-            uint32_t bb = 0;
-            for (int w = 0; w < r; ++w) {
-                const uint64_t d = (uint64_t)X[w] - P.m_words[w] - bb;
-                X[w] = (uint32_t)d;
-                bb = (uint32_t)(d >> 63);
-            }
-        }
-        for (int w = 0; w < r; ++w) R[(size_t)w * plane + e] = X[w];
+    switch (r) {
+        case 1: crt_tile<1>(P, R, plane, pitch, nro, logK); break;
+        case 2: crt_tile<2>(P, R, plane, pitch, nro, logK); break;
+        case 3: crt_tile<3>(P, R, plane, pitch, nro, logK); break;
+        case 4: crt_tile<4>(P, R, plane, pitch, nro, logK); break;
+        case 5: crt_tile<5>(P, R, plane, pitch, nro, logK); break;
+        default: crt_tile<6>(P, R, plane, pitch, nro, logK); break;
     }
     __syncthreads();
 
-    // Recombination c_i = sum_{j<2K} c_{i,j} 2^{Mj}, one warp per row,
-    // computed modulo 2^(32(lc+1)); the top limb is the sign word.
+    // Recombination c_i = sum_{j<2K} c_{i,j} 2^{Mj}, one warp per row, limbs
+    // 0..lc computed modulo 2^(32(lc+1)) (limb lc is the sign word), 32 limbs
+    // per step.  Each lane sums the pieces landing on its limb (a signed
+    // 64-bit P_q); P_q = t_q + 2^32 h_q.  Adding h_{q-1} to t_q leaves t'_q and
+    // a carry g_q in {-1, 0, 1}; the value is then sum t'_q 2^{32q} +
+    // sum_{g=1} 2^{32(q+1)} - sum_{g=-1} 2^{32(q+1)}, resolved as one
+    // addition and one subtraction, each by ballot carry-lookahead.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint32_t *st = reinterpret_cast<uint32_t *>(stage_base + (size_t)warp * stage_bytes);
-    int8_t *gg = reinterpret_cast<int8_t *>(st + lc1);
-    const int per = (lc1 + 31) / 32;
-    const int qb = lane * per, qe = min(qb + per, lc1);
-    for (int i2 = warp; i2 < Y2; i2 += nw) {
+    for (int i2 = warp; i2 < nro; i2 += nw) {
         const int64_t i = i1 + Y1 * (int64_t)i2;
-        if (i >= P.nc) continue;
-        const uint32_t *V = R + (size_t)i2 * twoK;
-        // phases 1-2: limb sums -> (t', g) with carries g in {-1,0,1}
-        int64_t hprev = qb < lc1 ? (limb_sum(V, plane, qb - 1, M, r, twoK) >> 32) : 0;
-        unsigned F = FN_IDENTITY;
-        for (int q = qb; q < qe; ++q) {
-            const int64_t Pq = limb_sum(V, plane, q, M, r, twoK);
-            const int64_t s = (int64_t)(uint32_t)Pq + hprev;
-            hprev = Pq >> 32;
-            const uint32_t tq = (uint32_t)s;
-            const int g = (int)(s >> 32);
-            st[q] = tq;
-            gg[q] = (int8_t)g;
-            const unsigned f = (unsigned)(g + (tq == 0u ? -1 : 0) + 1) | ((unsigned)(g + 1) << 2) |
-                               ((unsigned)(g + (tq == 0xffffffffu ? 1 : 0) + 1) << 4);
-            F = fn_compose(f, F);
-        }
-        // phase 3: warp scan of the carry functions
-        unsigned inc = F;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned o = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc = fn_compose(inc, o);
-        }
-        unsigned ex = __shfl_up_sync(0xffffffffu, inc, 1);
-        if (lane == 0) ex = FN_IDENTITY;
-        int cin = fn_apply(ex, 0);
-        for (int q = qb; q < qe; ++q) {
-            const uint32_t tq = st[q];
-            const int g = gg[q];
-            const int cout = g + ((tq == 0xffffffffu && cin == 1) ? 1 : 0) + ((tq == 0u && cin == -1) ? -1 : 0);
-            st[q] = tq + (uint32_t)cin;
-            cin = cout;
+        const uint32_t *V = R + (size_t)i2 * pitch;
+        int64_t h_last = 0;  // h of the previous chunk's last limb
+        int g_last = 0;      // g of the previous chunk's last limb
+        unsigned cplus = 0, cminus = 0;
+        int first_nz = lc1;  // lowest non-zero limb below the sign word
+        for (int q0 = 0; q0 < lc1; q0 += 32) {
+            const int q = q0 + lane;
+            const bool act = q < lc1;
+            const int64_t Pq = act ? limb_sum(V, plane, q, M, r, ranges[q]) : 0;
+            const int64_t h = Pq >> 32;
+            int64_t hprev = __shfl_up_sync(0xffffffffu, h, 1);
+            if (lane == 0) hprev = h_last;
+            const int64_t sum = (int64_t)(uint32_t)Pq + hprev;
+            const uint32_t tq = (uint32_t)sum;
+            const int g = (int)(sum >> 32);
+            int gprev = __shfl_up_sync(0xffffffffu, g, 1);
+            if (lane == 0) gprev = g_last;
+            h_last = __shfl_sync(0xffffffffu, h, 31);
+            g_last = __shfl_sync(0xffffffffu, g, 31);
+            // + 1 at every limb whose lower neighbour carried +1
+            const uint32_t gp = gprev == 1 ? 1u : 0u;
+            const unsigned cm = lookahead(__ballot_sync(0xffffffffu, act && gp && tq == 0xffffffffu),
+                                          __ballot_sync(0xffffffffu, act && tq + gp == 0xffffffffu), &cplus);
+            const uint32_t u = tq + gp + ((cm >> lane) & 1u);
+            // - 1 at every limb whose lower neighbour carried -1
+            const uint32_t gm = gprev == -1 ? 1u : 0u;
+            const unsigned bm = lookahead(__ballot_sync(0xffffffffu, act && gm && u == 0u),
+                                          __ballot_sync(0xffffffffu, act && u == gm), &cminus);
+            const uint32_t v = u - gm - ((bm >> lane) & 1u);
+            if (act) st[q] = v;
+            const unsigned nz = __ballot_sync(0xffffffffu, act && q < lc1 - 1 && v != 0u);
+            if (nz && first_nz == lc1) first_nz = q0 + __ffs(nz) - 1;
         }
         __syncwarp();
         const uint32_t top = st[lc1 - 1];
         const bool negative = top == 0xffffffffu;
         if (lane == 0 && top != 0u && !negative) atomicOr(P.err, ERRBIT_INTERNAL);
-        if (negative) {
-            // magnitude = -value over lc limbs: zero below the lowest non-zero
-            // limb f, -x at f, ~x above
-            int myf = 0x7fffffff;
-            for (int q = qb; q < min(qe, lc1 - 1); ++q)
-                if (st[q] != 0u) { myf = q; break; }
-            const unsigned m = __ballot_sync(0xffffffffu, myf != 0x7fffffff);
-            const int f = m ? __shfl_sync(0xffffffffu, myf, __ffs(m) - 1) : lc1;
-            for (int q = qb; q < min(qe, lc1 - 1); ++q) {
-                if (q == f) st[q] = 0u - st[q];
-                else if (q > f) st[q] = ~st[q];
-            }
-        }
-        __syncwarp();
         uint32_t *crow = c + (size_t)i * P.lc;
-        for (int q = lane; q < P.lc; q += 32) crow[q] = st[q];
+        for (int q = lane; q < P.lc; q += 32) {
+            uint32_t v = st[q];
+            if (negative) v = q < first_nz ? 0u : (q == first_nz ? 0u - v : ~v);
+            crow[q] = v;
+        }
         if (lane == 0) cn[i] = negative ? 1 : 0;
         __syncwarp();
     }

@@ -151,12 +151,13 @@ struct Tiles {
     size_t smem_fwd, smem_mid, smem_inv;
 };
 
-size_t fwd_smem(int64_t Y2, int K) { return (size_t)Y2 * K * 8 + (size_t)Y2 * 2 * K * 4; }
+size_t fwd_smem(int64_t Y2, int K) { return (size_t)Y2 * K * 8 + (size_t)Y2 * (2 * K + 1) * 4; }
 size_t inv_smem(int64_t Y2, int K, int r, int lc) {
     size_t stage = (size_t)(THREADS_INV / 32) * stage_bytes_per_warp(lc);
-    return (size_t)r * Y2 * 2 * K * 4 + stage;
+    size_t ranges = (((size_t)lc + 1) * 4 + 15) & ~(size_t)15;
+    return (size_t)r * Y2 * (2 * K + 1) * 4 + ranges + stage;
 }
-size_t mid_smem(int64_t Y1, int S) { return (size_t)2 * Y1 * S * 4; }
+size_t mid_smem(int64_t Y1, int S) { return ((size_t)2 * Y1 * (S + 1) + 16) * 4; }
 
 // Tile shapes: Y2 rows per forward/inverse tile, S columns per middle tile.
 bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force, Tiles &t) {

@@ -1,0 +1,238 @@
+// ntt_stages.cuh -- register-resident radix-R transform stages on
+// shared-memory tiles (R = 2, 4, 8, 16).
+//
+// A length-L transform is split into stages of radix R_1, R_2, ... (the
+// four-step factorisation applied recursively).  At a stage of radix R the
+// data are L/Lc independent sub-blocks of length Lc; with L' = Lc/R, thread
+// group (block, n1) gathers x_m = block[n1 + L' m] (m < R) into registers,
+// runs an R-point DFT there as radix-2 Gentleman-Sande butterflies with the
+// constants omega_R^j (held in registers), multiplies output k2 by
+// omega_Lc^{n1 k2}, and scatters it back.  The result is the same
+// bit-reversed-order DFT the plain radix-2 DIF gives, with one table
+// twiddle per element per stage instead of one per butterfly.  The inverse
+// stage is the exact mirror (inverse twiddle, then an R-point DIT DFT with
+// omega_R^{-1}), so forward followed by inverse is L times the identity.
+//
+// Element n of transform t lives at s[(t % tm) * ta + (t / tm) * tb + n * es]
+// (two-level transform index: e.g. row and half of a tile).  Consecutive
+// threads take consecutive t, so with an odd row pitch the gathers of a
+// warp hit distinct banks.
+#pragma once
+#include <stdint.h>
+
+#include "modarith.cuh"
+
+namespace ipm {
+
+template <int R>
+struct Roots {
+    uint2 w[R / 2 > 0 ? R / 2 : 1];  // omega_R^{+-j}, j < R/2
+};
+
+template <int R>
+__device__ __forceinline__ void load_roots(Roots<R> &rt, const uint2 *__restrict__ tab, int logT) {
+    constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
+#pragma unroll
+    for (int j = 0; j < R / 2; ++j) rt.w[j] = __ldg(tab + ((size_t)j << (logT - LR)));
+}
+
+template <int R>
+__host__ __device__ constexpr int brev_c(int m) {
+    int r = 0;
+    for (int b = 1, rb = R >> 1; b < R; b <<= 1, rb >>= 1)
+        if (m & b) r |= rb;
+    return r;
+}
+
+// (x, y) -> (x + y, x - y) with unit twiddle, values in [0, 2p).
+__device__ __forceinline__ void bf_unit(uint32_t &x, uint32_t &y, uint32_t p2) {
+    const uint32_t s = red(x + y, p2);
+    const uint32_t d = red(x - y + p2, p2);
+    x = s;
+    y = d;
+}
+
+// In-register DFT, natural order in, bit-reversed order out.
+template <int R>
+__device__ __forceinline__ void dft_dif(uint32_t (&x)[R], const Roots<R> &rt, uint32_t p, uint32_t p2) {
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                if (k == 0)
+                    bf_unit(x[b], x[b + h], p2);
+                else
+                    bf_dif(x[b + k], x[b + k + h], rt.w[k * (R / (2 * h))], p, p2);
+            }
+        }
+    }
+}
+
+// In-register inverse DFT (roots omega_R^{-j}), bit-reversed in, natural out.
+template <int R>
+__device__ __forceinline__ void dft_dit(uint32_t (&x)[R], const Roots<R> &rt, uint32_t p, uint32_t p2) {
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+        for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                if (k == 0)
+                    bf_unit(x[b], x[b + h], p2);
+                else
+                    bf_dit(x[b + k], x[b + k + h], rt.w[k * (R / (2 * h))], p, p2);
+            }
+        }
+    }
+}
+
+struct TileMap {
+    uint32_t *s;
+    int T;       // number of transforms
+    int tm;      // transforms per first-level group
+    int ta, tb;  // strides of t % tm and t / tm
+    int es;      // element stride
+};
+
+__device__ __forceinline__ int ilog2_if_pow2(int x) {
+    return (x & (x - 1)) ? -1 : 31 - __clz(x);
+}
+
+// Splits g into (t, rest) = (g % T, g / T) and returns the base address of
+// transform t; shifts when T and tm are powers of two.
+__device__ __forceinline__ uint32_t *group_base(const TileMap &m, int lT, int ltm, int g, int &rest) {
+    int t;
+    if (lT >= 0) {
+        t = g & (m.T - 1);
+        rest = g >> lT;
+    } else {
+        t = g % m.T;
+        rest = g / m.T;
+    }
+    const int t0 = ltm >= 0 ? (t & (m.tm - 1)) : t % m.tm;
+    const int t1 = ltm >= 0 ? (t >> ltm) : t / m.tm;
+    return m.s + t0 * m.ta + t1 * m.tb;
+}
+
+// One forward stage of radix R at sub-block length Lc = 2^logLc (L = 2^logL).
+// tw: table of omega_T^e (T = 2^logT), T a multiple of L.
+template <int R>
+__device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
+                                          const uint2 *__restrict__ tw, int logT, uint32_t p,
+                                          uint32_t p2) {
+    constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+    Roots<R> rt;
+    load_roots<R>(rt, tw, logT);
+    const int logLp = logLc - LR;
+    const int Lp = 1 << logLp;
+    const int total = M.T << (logL - LR);
+    const int tsh = logT - logLc;
+    const int lT = ilog2_if_pow2(M.T), ltm = ilog2_if_pow2(M.tm);
+    const int st = Lp * M.es;
+    for (int g = threadIdx.x; g < total; g += blockDim.x) {
+        int rest;
+        uint32_t *tb = group_base(M, lT, ltm, g, rest);
+        const int n1 = rest & (Lp - 1);
+        const int blk = rest >> logLp;
+        uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
+        // twiddles omega_Lc^{n1 k2} first: their latency hides behind the DFT
+        uint2 w[R];
+#pragma unroll
+        for (int m = 1; m < R; ++m) w[m] = __ldg(tw + ((size_t)(n1 * brev_c<R>(m)) << tsh));
+        uint32_t x[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = base[m * st];
+        dft_dif<R>(x, rt, p, p2);
+#pragma unroll
+        for (int m = 1; m < R; ++m) x[m] = shoup(x[m], w[m], p);
+#pragma unroll
+        for (int m = 0; m < R; ++m) base[m * st] = x[m];
+    }
+    __syncthreads();
+}
+
+template <int R>
+__device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
+                                          const uint2 *__restrict__ tw, int logT, uint32_t p,
+                                          uint32_t p2) {
+    constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+    Roots<R> rt;
+    load_roots<R>(rt, tw, logT);
+    const int logLp = logLc - LR;
+    const int Lp = 1 << logLp;
+    const int total = M.T << (logL - LR);
+    const int tsh = logT - logLc;
+    const int lT = ilog2_if_pow2(M.T), ltm = ilog2_if_pow2(M.tm);
+    const int st = Lp * M.es;
+    for (int g = threadIdx.x; g < total; g += blockDim.x) {
+        int rest;
+        uint32_t *tb = group_base(M, lT, ltm, g, rest);
+        const int n1 = rest & (Lp - 1);
+        const int blk = rest >> logLp;
+        uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
+        uint2 w[R];
+#pragma unroll
+        for (int m = 1; m < R; ++m) w[m] = __ldg(tw + ((size_t)(n1 * brev_c<R>(m)) << tsh));
+        uint32_t x[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = base[m * st];
+#pragma unroll
+        for (int m = 1; m < R; ++m) x[m] = shoup(x[m], w[m], p);
+        dft_dit<R>(x, rt, p, p2);
+#pragma unroll
+        for (int m = 0; m < R; ++m) base[m * st] = x[m];
+    }
+    __syncthreads();
+}
+
+// Radix sequence: logL is split into ceil(logL/4) stages of at most 4 bits
+// (radix 16), as even as possible, the larger stages first.
+__device__ __forceinline__ void stage_split(int logL, int &nst, int &base, int &extra) {
+    nst = (logL + 3) / 4;
+    base = nst ? logL / nst : 0;
+    extra = nst ? logL % nst : 0;
+}
+
+template <bool FWD>
+__device__ __forceinline__ void run_stage(int b, const TileMap &M, int logL, int logLc,
+                                          const uint2 *__restrict__ tw, int logT, uint32_t p,
+                                          uint32_t p2) {
+    switch (b) {
+        case 1: FWD ? stage_dif<2>(M, logL, logLc, tw, logT, p, p2) : stage_dit<2>(M, logL, logLc, tw, logT, p, p2); break;
+        case 2: FWD ? stage_dif<4>(M, logL, logLc, tw, logT, p, p2) : stage_dit<4>(M, logL, logLc, tw, logT, p, p2); break;
+        case 3: FWD ? stage_dif<8>(M, logL, logLc, tw, logT, p, p2) : stage_dit<8>(M, logL, logLc, tw, logT, p, p2); break;
+        default: FWD ? stage_dif<16>(M, logL, logLc, tw, logT, p, p2) : stage_dit<16>(M, logL, logLc, tw, logT, p, p2); break;
+    }
+}
+
+// Full forward transform of length 2^logL on every transform of the map
+// (natural order in, bit-reversed order out).  Values in [0, 2p).
+__device__ __forceinline__ void ntt_forward(const TileMap &M, int logL, const uint2 *__restrict__ tw,
+                                            int logT, uint32_t p, uint32_t p2) {
+    int nst, base, extra;
+    stage_split(logL, nst, base, extra);
+    int logLc = logL;
+    for (int i = 0; i < nst; ++i) {
+        const int b = base + (i < extra ? 1 : 0);
+        run_stage<true>(b, M, logL, logLc, tw, logT, p, p2);
+        logLc -= b;
+    }
+}
+
+// Inverse of ntt_forward up to the factor 2^logL (tw: inverse table): the
+// forward stages replayed backwards.
+__device__ __forceinline__ void ntt_inverse(const TileMap &M, int logL, const uint2 *__restrict__ tw,
+                                            int logT, uint32_t p, uint32_t p2) {
+    int nst, base, extra;
+    stage_split(logL, nst, base, extra);
+    int logLc = 0;
+    for (int i = nst - 1; i >= 0; --i) {
+        const int b = base + (i < extra ? 1 : 0);
+        logLc += b;
+        run_stage<false>(b, M, logL, logLc, tw, logT, p, p2);
+    }
+}
+
+}  // namespace ipm
