@@ -19,18 +19,12 @@ constexpr size_t SMEM_INV_MAX = 112 * 1024;
 constexpr size_t SMEM_MID_MAX = 200 * 1024;
 
 constexpr int THREADS_FWD = 256;
-constexpr int THREADS_MID = 512;
-constexpr int THREADS_INV = 256;
+constexpr int THREADS_MID = 1024;
+constexpr int THREADS_INV = 512;
 
 // Device error word bits.
 constexpr int ERRBIT_BOUND = 1;      // an input coefficient >= 2^bits
 constexpr int ERRBIT_INTERNAL = 2;   // recombination top limb not a sign word
-
-// Bytes of per-warp recombination staging in the inverse pass: lc+1
-// limbs (u32), rounded up to 16.
-__host__ __device__ inline size_t stage_bytes_per_warp(int lc) {
-    return (((size_t)lc + 1) * 4 + 15) & ~(size_t)15;
-}
 
 // Per-prime constants.  Twiddle tables hold (w, floor(w * 2^32 / p)) pairs
 // for Shoup's precomputed-quotient multiplication.

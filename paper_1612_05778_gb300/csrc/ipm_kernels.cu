@@ -335,7 +335,7 @@ __device__ __forceinline__ void crt_tile(const KParams &P, uint32_t *R, size_t p
     }
 }
 
-__global__ void __launch_bounds__(THREADS_INV)
+__global__ void __launch_bounds__(THREADS_INV, 2)
 k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *__restrict__ cn) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t i1 = blockIdx.x;
@@ -347,9 +347,6 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
     uint32_t *R = reinterpret_cast<uint32_t *>(smem);  // [r][Y2][pitch]
     const int lc1 = P.lc + 1;
     uint32_t *ranges = R + (size_t)r * plane;          // [lc1]
-    unsigned char *stage_base =
-        reinterpret_cast<unsigned char *>(ranges) + (((size_t)lc1 * 4 + 15) & ~(size_t)15);
-    const size_t stage_bytes = stage_bytes_per_warp(P.lc);
     for (int q = threadIdx.x; q < lc1; q += blockDim.x) ranges[q] = contrib_range(q, M, r, twoK);
 
     // rows i2 < nro are output coefficients (i = i1 + Y1*i2 < nc)
@@ -400,16 +397,20 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
     // 64-bit P_q); P_q = t_q + 2^32 h_q.  Adding h_{q-1} to t_q leaves t'_q and
     // a carry g_q in {-1, 0, 1}; the value is then sum t'_q 2^{32q} +
     // sum_{g=1} 2^{32(q+1)} - sum_{g=-1} 2^{32(q+1)}, resolved as one
-    // addition and one subtraction, each by ballot carry-lookahead.
+    // addition and one subtraction, each by ballot carry-lookahead.  Limbs go
+    // straight to the output in two's complement; a negative row is then
+    // turned into its magnitude in place (it is still in L2): zero below the
+    // lowest non-zero limb f, -x at f, ~x above.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t *st = reinterpret_cast<uint32_t *>(stage_base + (size_t)warp * stage_bytes);
     for (int i2 = warp; i2 < nro; i2 += nw) {
         const int64_t i = i1 + Y1 * (int64_t)i2;
         const uint32_t *V = R + (size_t)i2 * pitch;
+        uint32_t *crow = c + (size_t)i * P.lc;
         int64_t h_last = 0;  // h of the previous chunk's last limb
         int g_last = 0;      // g of the previous chunk's last limb
         unsigned cplus = 0, cminus = 0;
         int first_nz = lc1;  // lowest non-zero limb below the sign word
+        uint32_t top = 0;
         for (int q0 = 0; q0 < lc1; q0 += 32) {
             const int q = q0 + lane;
             const bool act = q < lc1;
@@ -434,22 +435,24 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
             const unsigned bm = lookahead(__ballot_sync(0xffffffffu, act && gm && u == 0u),
                                           __ballot_sync(0xffffffffu, act && u == gm), &cminus);
             const uint32_t v = u - gm - ((bm >> lane) & 1u);
-            if (act) st[q] = v;
-            const unsigned nz = __ballot_sync(0xffffffffu, act && q < lc1 - 1 && v != 0u);
+            if (q < lc1 - 1) crow[q] = v;
+            if (q == lc1 - 1) top = v;
+            const unsigned nz = __ballot_sync(0xffffffffu, q < lc1 - 1 && v != 0u);
             if (nz && first_nz == lc1) first_nz = q0 + __ffs(nz) - 1;
         }
-        __syncwarp();
-        const uint32_t top = st[lc1 - 1];
+        top = __shfl_sync(0xffffffffu, top, (lc1 - 1) & 31);
         const bool negative = top == 0xffffffffu;
-        if (lane == 0 && top != 0u && !negative) atomicOr(P.err, ERRBIT_INTERNAL);
-        uint32_t *crow = c + (size_t)i * P.lc;
-        for (int q = lane; q < P.lc; q += 32) {
-            uint32_t v = st[q];
-            if (negative) v = q < first_nz ? 0u : (q == first_nz ? 0u - v : ~v);
-            crow[q] = v;
+        if (lane == 0) {
+            if (top != 0u && !negative) atomicOr(P.err, ERRBIT_INTERNAL);
+            cn[i] = negative ? 1 : 0;
         }
-        if (lane == 0) cn[i] = negative ? 1 : 0;
-        __syncwarp();
+        if (negative) {
+            __syncwarp();  // the warp's own limb stores are visible to all its lanes
+            for (int q = first_nz + lane; q < P.lc; q += 32) {
+                const uint32_t v = crow[q];
+                crow[q] = q == first_nz ? 0u - v : ~v;
+            }
+        }
     }
 }
 

@@ -153,9 +153,8 @@ struct Tiles {
 
 size_t fwd_smem(int64_t Y2, int K) { return (size_t)Y2 * K * 8 + (size_t)Y2 * (2 * K + 1) * 4; }
 size_t inv_smem(int64_t Y2, int K, int r, int lc) {
-    size_t stage = (size_t)(THREADS_INV / 32) * stage_bytes_per_warp(lc);
     size_t ranges = (((size_t)lc + 1) * 4 + 15) & ~(size_t)15;
-    return (size_t)r * Y2 * (2 * K + 1) * 4 + ranges + stage;
+    return (size_t)r * Y2 * (2 * K + 1) * 4 + ranges;
 }
 size_t mid_smem(int64_t Y1, int S) { return ((size_t)2 * Y1 * (S + 1) + 16) * 4; }
 
