@@ -225,9 +225,27 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
 // Pass 3
 // ---------------------------------------------------------------------------
 
-// Contribution ranges of the recombination: limb q of sum_j V_j 2^{Mj}
-// receives pieces of V_j for jlo(q) <= j <= jhi(q) (V_j spans r words plus a
-// sign word above bit Mj).  Packed as jlo | count << 16.
+// Recombination tables.  Limb q of sum_j V_j 2^{Mj} receives word k of the
+// value V_j 2^{(Mj) mod 32} (r unsigned words and one signed top word, k =
+// 0..r) from every column j whose first limb floor(Mj/32) is q - k.  For
+// M >= 32 at most one column has a given first limb, so limb q's sources
+// are one column per k (or none): packed as 16-bit column indices, 0xffff
+// for none, eight slots per limb.  For M < 32 the general range form is
+// used: columns jlo .. jlo+count-1, packed as jlo | count << 16.
+__device__ __forceinline__ uint4 limb_sources(int q, int M, int r, int twoK) {
+    uint32_t slot[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) slot[k] = 0xffffu;
+    for (int k = 0; k <= r && k < 8; ++k) {
+        const int Q = q - k;  // first limb of the source column
+        if (Q < 0) break;
+        const int j = (32 * Q + M - 1) / M;  // smallest j with Mj >= 32Q
+        if (j < twoK && M * j < 32 * (Q + 1)) slot[k] = (uint32_t)j;
+    }
+    return make_uint4(slot[0] | slot[1] << 16, slot[2] | slot[3] << 16, slot[4] | slot[5] << 16,
+                      slot[6] | slot[7] << 16);
+}
+
 __device__ __forceinline__ uint32_t contrib_range(int q, int M, int r, int twoK) {
     const int jlo = q - r <= 0 ? 0 : (32 * (q - r) + M - 1) / M;
     int jhi = (32 * q + 31) / M;
@@ -236,25 +254,41 @@ __device__ __forceinline__ uint32_t contrib_range(int q, int M, int r, int twoK)
     return (uint32_t)jlo | ((uint32_t)cnt << 16);
 }
 
-// Sum of the contributions to limb q of sum_j V_j 2^{Mj}, where V_j is an
-// r-word two's-complement value at V[w * plane + j] (mod 2^(32(lc+1))).
-// V_j 2^sh is read as r unsigned words plus one signed top word.
-__device__ __forceinline__ int64_t limb_sum(const uint32_t *V, size_t plane, int q, int M, int r,
-                                            uint32_t range) {
+// Word k of V_j 2^sh: unsigned for k < r, the signed top word for k = r.
+template <int RR>
+__device__ __forceinline__ int64_t shifted_word(const uint32_t *V, int plane, int j, int k, int sh) {
+    if (k < RR) {
+        const uint32_t hi = V[k * plane + j];
+        const uint32_t lo = k > 0 ? V[(k - 1) * plane + j] : 0u;
+        return (int64_t)(sh ? __funnelshift_l(lo, hi, sh) : hi);
+    }
+    const int32_t top = (int32_t)V[(RR - 1) * plane + j];
+    return (int64_t)(sh ? (top >> (32 - sh)) : (top >> 31));
+}
+
+// Sum of the contributions to limb q (M >= 32: table form, unrolled).
+template <int RR>
+__device__ __forceinline__ int64_t limb_sum_tab(const uint32_t *V, int plane, int M, uint4 src) {
+    const uint32_t w[4] = {src.x, src.y, src.z, src.w};
+    int64_t acc = 0;
+#pragma unroll
+    for (int k = 0; k <= RR; ++k) {
+        const uint32_t j = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+        if (j != 0xffffu) acc += shifted_word<RR>(V, plane, (int)j, k, (int)((M * j) & 31));
+    }
+    return acc;
+}
+
+// Sum of the contributions to limb q (any M: range form).
+template <int RR>
+__device__ __forceinline__ int64_t limb_sum_rng(const uint32_t *V, int plane, int q, int M,
+                                                uint32_t range) {
     const int jlo = (int)(range & 0xffffu), cnt = (int)(range >> 16);
     int e = M * jlo;
     int64_t acc = 0;
     for (int n = 0; n < cnt; ++n, e += M) {
-        const int j = jlo + n;
-        const int k = q - (e >> 5), sh = e & 31;
-        if (k < r) {
-            const uint32_t hi = V[(size_t)k * plane + j];
-            const uint32_t lo = k > 0 ? V[(size_t)(k - 1) * plane + j] : 0u;
-            acc += (int64_t)(sh ? __funnelshift_l(lo, hi, sh) : hi);
-        } else {
-            const int32_t top = (int32_t)V[(size_t)(r - 1) * plane + j];
-            acc += (int64_t)(sh ? (top >> (32 - sh)) : (top >> 31));
-        }
+        const int k = q - (e >> 5);
+        if (k >= 0 && k <= RR) acc += shifted_word<RR>(V, plane, jlo + n, k, e & 31);
     }
     return acc;
 }
@@ -335,6 +369,80 @@ __device__ __forceinline__ void crt_tile(const KParams &P, uint32_t *R, size_t p
     }
 }
 
+// Recombination c_i = sum_{j<2K} c_{i,j} 2^{Mj}, one warp per row, limbs
+// 0..lc computed modulo 2^(32(lc+1)) (limb lc is the sign word), 32 limbs
+// per step.  Each lane sums the pieces landing on its limb (a signed 64-bit
+// P_q = t_q + 2^32 h_q).  Adding h_{q-1} to t_q leaves t'_q and a carry g_q
+// in {-1, 0, 1}; the value is then sum t'_q 2^{32q} + sum_{g=1} 2^{32(q+1)}
+// - sum_{g=-1} 2^{32(q+1)}, resolved as one addition and one subtraction,
+// each by ballot carry-lookahead.  Limbs go straight to the output in two's
+// complement; a negative row is then turned into its magnitude in place (it
+// is still in L2): zero below the lowest non-zero limb f, -x at f, ~x above.
+template <int RR>
+__device__ __forceinline__ void recombine_rows(const KParams &P, const uint32_t *R, int plane, int pitch,
+                                               const uint4 *sources, int nro, int64_t i1,
+                                               uint32_t *__restrict__ c, uint8_t *__restrict__ cn) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lc1 = P.lc + 1, M = P.M;
+    const bool tab = M >= 32;
+    for (int i2 = warp; i2 < nro; i2 += nw) {
+        const int64_t i = i1 + P.Y1 * (int64_t)i2;
+        const uint32_t *V = R + i2 * pitch;
+        uint32_t *crow = c + (size_t)i * P.lc;
+        int h_last = 0;  // h of the previous chunk's last limb
+        int g_last = 0;  // g of the previous chunk's last limb
+        unsigned cplus = 0, cminus = 0;
+        int first_nz = lc1;  // lowest non-zero limb below the sign word
+        uint32_t top = 0;
+        for (int q0 = 0; q0 < lc1; q0 += 32) {
+            const int q = q0 + lane;
+            const bool act = q < lc1;
+            int64_t Pq = 0;
+            if (act) {
+                const uint4 src = sources[q];
+                Pq = tab ? limb_sum_tab<RR>(V, plane, M, src) : limb_sum_rng<RR>(V, plane, q, M, src.x);
+            }
+            const int h = (int)(Pq >> 32);  // |h| < 2^8
+            int hprev = __shfl_up_sync(0xffffffffu, h, 1);
+            if (lane == 0) hprev = h_last;
+            const int64_t sum = (int64_t)(uint32_t)Pq + hprev;
+            const uint32_t tq = (uint32_t)sum;
+            const int g = (int)(sum >> 32);
+            int gprev = __shfl_up_sync(0xffffffffu, g, 1);
+            if (lane == 0) gprev = g_last;
+            h_last = __shfl_sync(0xffffffffu, h, 31);
+            g_last = __shfl_sync(0xffffffffu, g, 31);
+            // + 1 at every limb whose lower neighbour carried +1
+            const uint32_t gp = gprev == 1 ? 1u : 0u;
+            const unsigned cm = lookahead(__ballot_sync(0xffffffffu, act && gp && tq == 0xffffffffu),
+                                          __ballot_sync(0xffffffffu, act && tq + gp == 0xffffffffu), &cplus);
+            const uint32_t u = tq + gp + ((cm >> lane) & 1u);
+            // - 1 at every limb whose lower neighbour carried -1
+            const uint32_t gm = gprev == -1 ? 1u : 0u;
+            const unsigned bm = lookahead(__ballot_sync(0xffffffffu, act && gm && u == 0u),
+                                          __ballot_sync(0xffffffffu, act && u == gm), &cminus);
+            const uint32_t v = u - gm - ((bm >> lane) & 1u);
+            if (q < lc1 - 1) crow[q] = v;
+            if (q == lc1 - 1) top = v;
+            const unsigned nz = __ballot_sync(0xffffffffu, q < lc1 - 1 && v != 0u);
+            if (nz && first_nz == lc1) first_nz = q0 + __ffs(nz) - 1;
+        }
+        top = __shfl_sync(0xffffffffu, top, (lc1 - 1) & 31);
+        const bool negative = top == 0xffffffffu;
+        if (lane == 0) {
+            if (top != 0u && !negative) atomicOr(P.err, ERRBIT_INTERNAL);
+            cn[i] = negative ? 1 : 0;
+        }
+        if (negative) {
+            __syncwarp();  // the warp's own limb stores are visible to all its lanes
+            for (int q = first_nz + lane; q < P.lc; q += 32) {
+                const uint32_t v = crow[q];
+                crow[q] = q == first_nz ? 0u - v : ~v;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(THREADS_INV, 2)
 k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *__restrict__ cn) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -346,8 +454,9 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
     const size_t plane = (size_t)Y2 * pitch;
     uint32_t *R = reinterpret_cast<uint32_t *>(smem);  // [r][Y2][pitch]
     const int lc1 = P.lc + 1;
-    uint32_t *ranges = R + (size_t)r * plane;          // [lc1]
-    for (int q = threadIdx.x; q < lc1; q += blockDim.x) ranges[q] = contrib_range(q, M, r, twoK);
+    uint4 *sources = reinterpret_cast<uint4 *>(smem + (((size_t)r * plane * 4 + 15) & ~(size_t)15));  // [lc1]
+    for (int q = threadIdx.x; q < lc1; q += blockDim.x)
+        sources[q] = M >= 32 ? limb_sources(q, M, r, twoK) : make_uint4(contrib_range(q, M, r, twoK), 0, 0, 0);
 
     // rows i2 < nro are output coefficients (i = i1 + Y1*i2 < nc)
     const int nro = i1 < P.nc ? (int)min((int64_t)Y2, (P.nc - i1 + Y1 - 1) / Y1) : 0;
@@ -401,58 +510,13 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
     // straight to the output in two's complement; a negative row is then
     // turned into its magnitude in place (it is still in L2): zero below the
     // lowest non-zero limb f, -x at f, ~x above.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i2 = warp; i2 < nro; i2 += nw) {
-        const int64_t i = i1 + Y1 * (int64_t)i2;
-        const uint32_t *V = R + (size_t)i2 * pitch;
-        uint32_t *crow = c + (size_t)i * P.lc;
-        int64_t h_last = 0;  // h of the previous chunk's last limb
-        int g_last = 0;      // g of the previous chunk's last limb
-        unsigned cplus = 0, cminus = 0;
-        int first_nz = lc1;  // lowest non-zero limb below the sign word
-        uint32_t top = 0;
-        for (int q0 = 0; q0 < lc1; q0 += 32) {
-            const int q = q0 + lane;
-            const bool act = q < lc1;
-            const int64_t Pq = act ? limb_sum(V, plane, q, M, r, ranges[q]) : 0;
-            const int64_t h = Pq >> 32;
-            int64_t hprev = __shfl_up_sync(0xffffffffu, h, 1);
-            if (lane == 0) hprev = h_last;
-            const int64_t sum = (int64_t)(uint32_t)Pq + hprev;
-            const uint32_t tq = (uint32_t)sum;
-            const int g = (int)(sum >> 32);
-            int gprev = __shfl_up_sync(0xffffffffu, g, 1);
-            if (lane == 0) gprev = g_last;
-            h_last = __shfl_sync(0xffffffffu, h, 31);
-            g_last = __shfl_sync(0xffffffffu, g, 31);
-            // + 1 at every limb whose lower neighbour carried +1
-            const uint32_t gp = gprev == 1 ? 1u : 0u;
-            const unsigned cm = lookahead(__ballot_sync(0xffffffffu, act && gp && tq == 0xffffffffu),
-                                          __ballot_sync(0xffffffffu, act && tq + gp == 0xffffffffu), &cplus);
-            const uint32_t u = tq + gp + ((cm >> lane) & 1u);
-            // - 1 at every limb whose lower neighbour carried -1
-            const uint32_t gm = gprev == -1 ? 1u : 0u;
-            const unsigned bm = lookahead(__ballot_sync(0xffffffffu, act && gm && u == 0u),
-                                          __ballot_sync(0xffffffffu, act && u == gm), &cminus);
-            const uint32_t v = u - gm - ((bm >> lane) & 1u);
-            if (q < lc1 - 1) crow[q] = v;
-            if (q == lc1 - 1) top = v;
-            const unsigned nz = __ballot_sync(0xffffffffu, q < lc1 - 1 && v != 0u);
-            if (nz && first_nz == lc1) first_nz = q0 + __ffs(nz) - 1;
-        }
-        top = __shfl_sync(0xffffffffu, top, (lc1 - 1) & 31);
-        const bool negative = top == 0xffffffffu;
-        if (lane == 0) {
-            if (top != 0u && !negative) atomicOr(P.err, ERRBIT_INTERNAL);
-            cn[i] = negative ? 1 : 0;
-        }
-        if (negative) {
-            __syncwarp();  // the warp's own limb stores are visible to all its lanes
-            for (int q = first_nz + lane; q < P.lc; q += 32) {
-                const uint32_t v = crow[q];
-                crow[q] = q == first_nz ? 0u - v : ~v;
-            }
-        }
+    switch (r) {
+        case 1: recombine_rows<1>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        case 2: recombine_rows<2>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        case 3: recombine_rows<3>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        case 4: recombine_rows<4>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        case 5: recombine_rows<5>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        default: recombine_rows<6>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
     }
 }
 

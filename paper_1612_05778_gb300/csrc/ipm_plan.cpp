@@ -153,8 +153,8 @@ struct Tiles {
 
 size_t fwd_smem(int64_t Y2, int K) { return (size_t)Y2 * K * 8 + (size_t)Y2 * (2 * K + 1) * 4; }
 size_t inv_smem(int64_t Y2, int K, int r, int lc) {
-    size_t ranges = (((size_t)lc + 1) * 4 + 15) & ~(size_t)15;
-    return (size_t)r * Y2 * (2 * K + 1) * 4 + ranges;
+    size_t sources = ((size_t)lc + 1) * 16;  // one uint4 per limb
+    return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources;
 }
 size_t mid_smem(int64_t Y1, int S) { return ((size_t)2 * Y1 * (S + 1) + 16) * 4; }
 

@@ -137,16 +137,22 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
         const int n1 = rest & (Lp - 1);
         const int blk = rest >> logLp;
         uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
-        // twiddles omega_Lc^{n1 k2} first: their latency hides behind the DFT
-        uint2 w[R];
-#pragma unroll
-        for (int m = 1; m < R; ++m) w[m] = __ldg(tw + ((size_t)(n1 * brev_c<R>(m)) << tsh));
         uint32_t x[R];
+        if (Lp > 1) {
+            // twiddles omega_Lc^{n1 k2} first: their latency hides behind the DFT
+            uint2 w[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) x[m] = base[m * st];
-        dft_dif<R>(x, rt, p, p2);
+            for (int m = 1; m < R; ++m) w[m] = __ldg(tw + ((uint32_t)(n1 * brev_c<R>(m)) << tsh));
 #pragma unroll
-        for (int m = 1; m < R; ++m) x[m] = shoup(x[m], w[m], p);
+            for (int m = 0; m < R; ++m) x[m] = base[m * st];
+            dft_dif<R>(x, rt, p, p2);
+#pragma unroll
+            for (int m = 1; m < R; ++m) x[m] = shoup(x[m], w[m], p);
+        } else {  // last stage: every twiddle is 1
+#pragma unroll
+            for (int m = 0; m < R; ++m) x[m] = base[m * st];
+            dft_dif<R>(x, rt, p, p2);
+        }
 #pragma unroll
         for (int m = 0; m < R; ++m) base[m * st] = x[m];
     }
@@ -172,14 +178,19 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
         const int n1 = rest & (Lp - 1);
         const int blk = rest >> logLp;
         uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
-        uint2 w[R];
-#pragma unroll
-        for (int m = 1; m < R; ++m) w[m] = __ldg(tw + ((size_t)(n1 * brev_c<R>(m)) << tsh));
         uint32_t x[R];
+        if (Lp > 1) {
+            uint2 w[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) x[m] = base[m * st];
+            for (int m = 1; m < R; ++m) w[m] = __ldg(tw + ((uint32_t)(n1 * brev_c<R>(m)) << tsh));
 #pragma unroll
-        for (int m = 1; m < R; ++m) x[m] = shoup(x[m], w[m], p);
+            for (int m = 0; m < R; ++m) x[m] = base[m * st];
+#pragma unroll
+            for (int m = 1; m < R; ++m) x[m] = shoup(x[m], w[m], p);
+        } else {  // first inverse stage: every twiddle is 1
+#pragma unroll
+            for (int m = 0; m < R; ++m) x[m] = base[m * st];
+        }
         dft_dit<R>(x, rt, p, p2);
 #pragma unroll
         for (int m = 0; m < R; ++m) base[m * st] = x[m];

@@ -99,7 +99,7 @@ def test_small_dense_workload_full():
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(K=16), dict(K=32), dict(K=8, M=40),
-                                dict(r=4), dict(r=5), dict(y2=1), dict(y2=64), dict(s=1),
+                                dict(r=4), dict(r=5), dict(r=6), dict(y2=1), dict(y2=64), dict(s=1),
                                 dict(K=64, y2=4, s=2), dict(K=8, M=62), dict(K=256)])
 def test_plan_invariance(kw):
     """Every valid (K, M, r, tiles) gives byte-identical output."""
