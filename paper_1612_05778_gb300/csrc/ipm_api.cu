@@ -99,11 +99,11 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
         if (st != IPM_OK) { free_plan(plan); return st; }
         zmax = std::max(zmax, plan->shapes[(size_t)i].z_words);
     }
-    // Tables are shared between shapes with the same (Y, K, r): the primes
-    // are always the r largest of the table, so these fix every entry.
-    std::map<std::tuple<int64_t, int32_t, int32_t>, const uint2 *> cache;
+    // Tables are shared between shapes with the same (Y, Y1, K, r): the
+    // primes are always the r largest of the table, so these fix every entry.
+    std::map<std::tuple<int64_t, int64_t, int32_t, int32_t>, const uint2 *> cache;
     for (auto &sp : plan->shapes) {
-        auto key = std::make_tuple(sp.kp.Y, sp.kp.K, sp.kp.r);
+        auto key = std::make_tuple(sp.kp.Y, sp.kp.Y1, sp.kp.K, sp.kp.r);
         std::vector<uint2> host((size_t)sp.kp.r * sp.table_words);
         build_tables(sp, host.data());  // also fills the scalar constants
         const uint2 *dtab = nullptr;
@@ -120,11 +120,15 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
             dtab = (const uint2 *)d;
             cache[key] = dtab;
         }
-        const TableLayout L = table_layout(sp.kp.Y, sp.kp.K);
+        const TableLayout L = table_layout(sp.kp.Y, sp.kp.Y1, sp.kp.K);
         for (int t = 0; t < sp.kp.r; ++t) {
             const uint2 *blk = dtab + (size_t)t * L.total;
             sp.kp.pc[t].ty_f = blk + L.ty_f;
             sp.kp.pc[t].ty_i = blk + L.ty_i;
+            sp.kp.pc[t].t1_f = blk + L.t1_f;
+            sp.kp.pc[t].t1_i = blk + L.t1_i;
+        sp.kp.pc[t].t1_f = blk + L.t1_f;
+        sp.kp.pc[t].t1_i = blk + L.t1_i;
             sp.kp.pc[t].tx_f = blk + L.tx_f;
             sp.kp.pc[t].tx_i = blk + L.tx_i;
             sp.kp.pc[t].untw = blk + L.untw;

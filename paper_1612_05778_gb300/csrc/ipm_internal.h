@@ -39,6 +39,8 @@ struct PrimeConst {
     uint32_t scale_s;
     const uint2 *ty_f; // omega_Y^e,     e < Y   (forward y twiddles)
     const uint2 *ty_i; // omega_Y^{-e},  e < Y   (inverse y twiddles)
+    const uint2 *t1_f; // omega_Y1^e,    e < Y1  (compact table of the middle pass)
+    const uint2 *t1_i; // omega_Y1^{-e}, e < Y1
     const uint2 *tx_f; // theta^e,       e < 2K  (theta: primitive 2K-th root)
     const uint2 *tx_i; // theta^{-e},    e < 2K
     const uint2 *untw; // scale * theta^{-j}, j < K
@@ -80,9 +82,9 @@ void build_tables(ShapePlan &sp, uint2 *tab);
 
 // Table block offsets (uint2 entries) within one prime's block.
 struct TableLayout {
-    size_t ty_f, ty_i, tx_f, tx_i, untw, total;
+    size_t ty_f, ty_i, t1_f, t1_i, tx_f, tx_i, untw, total;
 };
-TableLayout table_layout(int64_t Y, int32_t K);
+TableLayout table_layout(int64_t Y, int64_t Y1, int32_t K);
 
 // Kernel launchers (ipm_kernels.cu).
 int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint8_t *an,

@@ -189,13 +189,19 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
     const int pitch = S + 1;  // odd pitch for conflict-free strided gathers
     const int twoK = 2 * P.K;
     const int Y1 = (int)P.Y1;
-    uint32_t *A = reinterpret_cast<uint32_t *>(smem);  // [Y1][pitch]
+    uint2 *twf = reinterpret_cast<uint2 *>(smem);       // omega_Y1^e, e < Y1
+    uint2 *twi = twf + Y1;                              // omega_Y1^{-e}
+    uint32_t *A = reinterpret_cast<uint32_t *>(twi + Y1);  // [Y1][pitch]
     uint32_t *B = A + (size_t)Y1 * pitch + 16;          // [Y1][pitch], shifted 16 banks
     const PrimeConst &pc = P.pc[t];
     const uint32_t p = pc.p, p2 = pc.p2;
     uint32_t *ZA = P.Z + (size_t)(t * 2 + 0) * (size_t)P.Y * twoK;
     const uint32_t *ZB = P.Z + (size_t)(t * 2 + 1) * (size_t)P.Y * twoK;
     const size_t base = (size_t)pos * Y1 * twoK + (size_t)cs * S;
+    for (int e = threadIdx.x; e < Y1; e += blockDim.x) {
+        twf[e] = __ldg(pc.t1_f + e);
+        twi[e] = __ldg(pc.t1_i + e);
+    }
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
         const int i1 = e >> logS, c = e & (S - 1);
         const size_t g = base + (size_t)i1 * twoK + c;
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
     __syncthreads();
     // y step C (omega_Y1 = omega_Y^Y2) on the S columns of A and of B
     const TileMap both{A, 2 * S, S, 1, (int)(B - A), pitch};
-    ntt_forward(both, P.logY1, pc.ty_f, P.logY, p, p2);
+    ntt_forward<true>(both, P.logY1, twf, P.logY1, p, p2);
     // pointwise product in Montgomery form: A*B*2^-32 (the 2^32 is put back
     // by the scale factor of the inverse pass)
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
@@ -214,7 +220,7 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
     }
     __syncthreads();
     const TileMap am{A, S, S, 1, 0, pitch};
-    ntt_inverse(am, P.logY1, pc.ty_i, P.logY, p, p2);
+    ntt_inverse<true>(am, P.logY1, twi, P.logY1, p, p2);
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
         const int i1 = e >> logS, c = e & (S - 1);
         ZA[base + (size_t)i1 * twoK + c] = red(A[i1 * pitch + c], p);

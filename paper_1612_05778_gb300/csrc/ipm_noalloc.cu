@@ -93,11 +93,13 @@ extern "C" ipm_status ipm_mul_noalloc(const ipm_shape *shape, const uint32_t *a,
         cudaSuccess)
         return IPM_ERR_CUDA;
     if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return IPM_ERR_CUDA;
-    const ipm::TableLayout L = ipm::table_layout(sp.kp.Y, sp.kp.K);
+    const ipm::TableLayout L = ipm::table_layout(sp.kp.Y, sp.kp.Y1, sp.kp.K);
     for (int t = 0; t < sp.kp.r; ++t) {
         const uint2 *blk = dtab + (size_t)t * L.total;
         sp.kp.pc[t].ty_f = blk + L.ty_f;
         sp.kp.pc[t].ty_i = blk + L.ty_i;
+        sp.kp.pc[t].t1_f = blk + L.t1_f;
+        sp.kp.pc[t].t1_i = blk + L.t1_i;
         sp.kp.pc[t].tx_f = blk + L.tx_f;
         sp.kp.pc[t].tx_i = blk + L.tx_i;
         sp.kp.pc[t].untw = blk + L.untw;

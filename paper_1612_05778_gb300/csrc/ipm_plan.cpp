@@ -156,7 +156,7 @@ size_t inv_smem(int64_t Y2, int K, int r, int lc) {
     size_t sources = ((size_t)lc + 1) * 16;  // one uint4 per limb
     return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources;
 }
-size_t mid_smem(int64_t Y1, int S) { return ((size_t)2 * Y1 * (S + 1) + 16) * 4; }
+size_t mid_smem(int64_t Y1, int S) { return ((size_t)2 * Y1 * (S + 1) + 16) * 4 + (size_t)2 * Y1 * 8; }
 
 // Tile shapes: Y2 rows per forward/inverse tile, S columns per middle tile.
 bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force, Tiles &t) {
@@ -195,11 +195,13 @@ bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force
 
 }  // namespace
 
-TableLayout table_layout(int64_t Y, int32_t K) {
+TableLayout table_layout(int64_t Y, int64_t Y1, int32_t K) {
     TableLayout L;
     L.ty_f = 0;
     L.ty_i = L.ty_f + (size_t)Y;
-    L.tx_f = L.ty_i + (size_t)Y;
+    L.t1_f = L.ty_i + (size_t)Y;
+    L.t1_i = L.t1_f + (size_t)Y1;
+    L.tx_f = L.t1_i + (size_t)Y1;
     L.tx_i = L.tx_f + 2 * (size_t)K;
     L.untw = L.tx_i + 2 * (size_t)K;
     L.total = L.untw + (size_t)K;
@@ -277,7 +279,7 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
         s.smem_mid = tl.smem_mid;
         s.smem_inv = tl.smem_inv;
         s.z_words = (size_t)r * 2 * (size_t)Y * 2 * K;
-        s.table_words = table_layout(Y, K).total;
+        s.table_words = table_layout(Y, Y / tl.Y2, K).total;
         I.workspace_bytes = s.z_words * 4 + (size_t)r * s.table_words * 8;
         KParams &kp = s.kp;
         std::memset(&kp, 0, sizeof(kp));
@@ -299,7 +301,7 @@ void build_tables(ShapePlan &sp, uint2 *tab) {
     KParams &kp = sp.kp;
     const int64_t Y = kp.Y;
     const int K = kp.K;
-    const TableLayout L = table_layout(Y, K);
+    const TableLayout L = table_layout(Y, kp.Y1, K);
     for (int t = 0; t < kp.r; ++t) {
         const uint32_t p = sp.info.primes[t];
         uint2 *blk = tab + (size_t)t * L.total;
@@ -312,6 +314,10 @@ void build_tables(ShapePlan &sp, uint2 *tab) {
             blk[L.ty_i + e] = make_uint2((uint32_t)xi, shoup_q((uint32_t)xi, p));
             x = x * w % p;
             xi = xi * wi % p;
+        }
+        for (int64_t e = 0; e < kp.Y1; ++e) {  // omega_Y1 = omega_Y^Y2
+            blk[L.t1_f + e] = blk[L.ty_f + e * kp.Y2];
+            blk[L.t1_i + e] = blk[L.ty_i + e * kp.Y2];
         }
         // scale = 2^32 * (2 Y K)^{-1} mod p
         const uint64_t two32 = (1ull << 32) % p;

@@ -29,11 +29,21 @@ struct Roots {
     uint2 w[R / 2 > 0 ? R / 2 : 1];  // omega_R^{+-j}, j < R/2
 };
 
-template <int R>
+// Twiddle-table read: SM = the table lives in shared memory, else in global
+// memory (read through the non-coherent cache).
+template <bool SM>
+__device__ __forceinline__ uint2 tload(const uint2 *p) {
+    if constexpr (SM)
+        return *p;
+    else
+        return __ldg(p);
+}
+
+template <int R, bool SM>
 __device__ __forceinline__ void load_roots(Roots<R> &rt, const uint2 *__restrict__ tab, int logT) {
     constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
 #pragma unroll
-    for (int j = 0; j < R / 2; ++j) rt.w[j] = __ldg(tab + ((size_t)j << (logT - LR)));
+    for (int j = 0; j < R / 2; ++j) rt.w[j] = tload<SM>(tab + ((uint32_t)j << (logT - LR)));
 }
 
 template <int R>
@@ -118,13 +128,13 @@ __device__ __forceinline__ uint32_t *group_base(const TileMap &m, int lT, int lt
 
 // One forward stage of radix R at sub-block length Lc = 2^logLc (L = 2^logL).
 // tw: table of omega_T^e (T = 2^logT), T a multiple of L.
-template <int R>
+template <int R, bool SM>
 __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
                                           uint32_t p2) {
     constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
     Roots<R> rt;
-    load_roots<R>(rt, tw, logT);
+    load_roots<R, SM>(rt, tw, logT);
     const int logLp = logLc - LR;
     const int Lp = 1 << logLp;
     const int total = M.T << (logL - LR);
@@ -142,7 +152,7 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
             // twiddles omega_Lc^{n1 k2} first: their latency hides behind the DFT
             uint2 w[R];
 #pragma unroll
-            for (int m = 1; m < R; ++m) w[m] = __ldg(tw + ((uint32_t)(n1 * brev_c<R>(m)) << tsh));
+            for (int m = 1; m < R; ++m) w[m] = tload<SM>(tw + ((uint32_t)(n1 * brev_c<R>(m)) << tsh));
 #pragma unroll
             for (int m = 0; m < R; ++m) x[m] = base[m * st];
             dft_dif<R>(x, rt, p, p2);
@@ -159,13 +169,13 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
     __syncthreads();
 }
 
-template <int R>
+template <int R, bool SM>
 __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
                                           uint32_t p2) {
     constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
     Roots<R> rt;
-    load_roots<R>(rt, tw, logT);
+    load_roots<R, SM>(rt, tw, logT);
     const int logLp = logLc - LR;
     const int Lp = 1 << logLp;
     const int total = M.T << (logL - LR);
@@ -182,7 +192,7 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
         if (Lp > 1) {
             uint2 w[R];
 #pragma unroll
-            for (int m = 1; m < R; ++m) w[m] = __ldg(tw + ((uint32_t)(n1 * brev_c<R>(m)) << tsh));
+            for (int m = 1; m < R; ++m) w[m] = tload<SM>(tw + ((uint32_t)(n1 * brev_c<R>(m)) << tsh));
 #pragma unroll
             for (int m = 0; m < R; ++m) x[m] = base[m * st];
 #pragma unroll
@@ -206,20 +216,21 @@ __device__ __forceinline__ void stage_split(int logL, int &nst, int &base, int &
     extra = nst ? logL % nst : 0;
 }
 
-template <bool FWD>
+template <bool FWD, bool SM>
 __device__ __forceinline__ void run_stage(int b, const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
                                           uint32_t p2) {
     switch (b) {
-        case 1: FWD ? stage_dif<2>(M, logL, logLc, tw, logT, p, p2) : stage_dit<2>(M, logL, logLc, tw, logT, p, p2); break;
-        case 2: FWD ? stage_dif<4>(M, logL, logLc, tw, logT, p, p2) : stage_dit<4>(M, logL, logLc, tw, logT, p, p2); break;
-        case 3: FWD ? stage_dif<8>(M, logL, logLc, tw, logT, p, p2) : stage_dit<8>(M, logL, logLc, tw, logT, p, p2); break;
-        default: FWD ? stage_dif<16>(M, logL, logLc, tw, logT, p, p2) : stage_dit<16>(M, logL, logLc, tw, logT, p, p2); break;
+        case 1: FWD ? stage_dif<2, SM>(M, logL, logLc, tw, logT, p, p2) : stage_dit<2, SM>(M, logL, logLc, tw, logT, p, p2); break;
+        case 2: FWD ? stage_dif<4, SM>(M, logL, logLc, tw, logT, p, p2) : stage_dit<4, SM>(M, logL, logLc, tw, logT, p, p2); break;
+        case 3: FWD ? stage_dif<8, SM>(M, logL, logLc, tw, logT, p, p2) : stage_dit<8, SM>(M, logL, logLc, tw, logT, p, p2); break;
+        default: FWD ? stage_dif<16, SM>(M, logL, logLc, tw, logT, p, p2) : stage_dit<16, SM>(M, logL, logLc, tw, logT, p, p2); break;
     }
 }
 
 // Full forward transform of length 2^logL on every transform of the map
 // (natural order in, bit-reversed order out).  Values in [0, 2p).
+template <bool SM = false>
 __device__ __forceinline__ void ntt_forward(const TileMap &M, int logL, const uint2 *__restrict__ tw,
                                             int logT, uint32_t p, uint32_t p2) {
     int nst, base, extra;
@@ -227,13 +238,14 @@ __device__ __forceinline__ void ntt_forward(const TileMap &M, int logL, const ui
     int logLc = logL;
     for (int i = 0; i < nst; ++i) {
         const int b = base + (i < extra ? 1 : 0);
-        run_stage<true>(b, M, logL, logLc, tw, logT, p, p2);
+        run_stage<true, SM>(b, M, logL, logLc, tw, logT, p, p2);
         logLc -= b;
     }
 }
 
 // Inverse of ntt_forward up to the factor 2^logL (tw: inverse table): the
 // forward stages replayed backwards.
+template <bool SM = false>
 __device__ __forceinline__ void ntt_inverse(const TileMap &M, int logL, const uint2 *__restrict__ tw,
                                             int logT, uint32_t p, uint32_t p2) {
     int nst, base, extra;
@@ -242,7 +254,7 @@ __device__ __forceinline__ void ntt_inverse(const TileMap &M, int logL, const ui
     for (int i = nst - 1; i >= 0; --i) {
         const int b = base + (i < extra ? 1 : 0);
         logLc += b;
-        run_stage<false>(b, M, logL, logLc, tw, logT, p, p2);
+        run_stage<false, SM>(b, M, logL, logLc, tw, logT, p, p2);
     }
 }
 
