@@ -198,20 +198,31 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
     uint32_t *ZA = P.Z + (size_t)(t * 2 + 0) * (size_t)P.Y * twoK;
     const uint32_t *ZB = P.Z + (size_t)(t * 2 + 1) * (size_t)P.Y * twoK;
     const size_t base = (size_t)pos * Y1 * twoK + (size_t)cs * S;
+    // A's slice, then B's, as two asynchronous copy groups: B is still in
+    // flight while A is transformed
+    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+        const int i1 = e >> logS, c = e & (S - 1);
+        cp_async4(A + i1 * pitch + c, ZA + base + (size_t)i1 * twoK + c);
+    }
+    cp_async_commit();
+    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+        const int i1 = e >> logS, c = e & (S - 1);
+        cp_async4(B + i1 * pitch + c, ZB + base + (size_t)i1 * twoK + c);
+    }
+    cp_async_commit();
     for (int e = threadIdx.x; e < Y1; e += blockDim.x) {
         twf[e] = __ldg(pc.t1_f + e);
         twi[e] = __ldg(pc.t1_i + e);
     }
-    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
-        const int i1 = e >> logS, c = e & (S - 1);
-        const size_t g = base + (size_t)i1 * twoK + c;
-        A[i1 * pitch + c] = ZA[g];
-        B[i1 * pitch + c] = ZB[g];
-    }
+    cp_async_wait<1>();
     __syncthreads();
-    // y step C (omega_Y1 = omega_Y^Y2) on the S columns of A and of B
-    const TileMap both{A, 2 * S, S, 1, (int)(B - A), pitch};
-    ntt_forward<true>(both, P.logY1, twf, P.logY1, p, p2);
+    // y step C (omega_Y1 = omega_Y^Y2) on the S columns of A, then of B
+    const TileMap am{A, S, S, 1, 0, pitch};
+    ntt_forward<true>(am, P.logY1, twf, P.logY1, p, p2);
+    cp_async_wait<0>();
+    __syncthreads();
+    const TileMap bm{B, S, S, 1, 0, pitch};
+    ntt_forward<true>(bm, P.logY1, twf, P.logY1, p, p2);
     // pointwise product in Montgomery form: A*B*2^-32 (the 2^32 is put back
     // by the scale factor of the inverse pass)
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
@@ -219,7 +230,6 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
         A[i] = montmul(A[i], B[i], p, pc.mont);
     }
     __syncthreads();
-    const TileMap am{A, S, S, 1, 0, pitch};
     ntt_inverse<true>(am, P.logY1, twi, P.logY1, p, p2);
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
         const int i1 = e >> logS, c = e & (S - 1);
@@ -466,16 +476,34 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
 
     // rows i2 < nro are output coefficients (i = i1 + Y1*i2 < nc)
     const int nro = i1 < P.nc ? (int)min((int64_t)Y2, (P.nc - i1 + Y1 - 1) / Y1) : 0;
+    // every prime's rows (k2, i1) requested at once, one copy group per prime
+    for (int t = 0; t < r; ++t) {
+        const uint32_t *Zt = P.Z + (size_t)(t * 2) * (size_t)P.Y * twoK;
+        for (int e = threadIdx.x; e < Y2 * twoK; e += blockDim.x) {
+            const int pos = e >> (logK + 1), col = e & (twoK - 1);
+            cp_async4(R + (size_t)t * plane + (size_t)pos * pitch + col, Zt + ((size_t)pos * Y1 + i1) * twoK + col);
+        }
+        cp_async_commit();
+    }
     for (int t = 0; t < r; ++t) {
         const PrimeConst &pc = P.pc[t];
         const uint32_t p = pc.p, p2 = pc.p2;
         uint32_t *Rt = R + (size_t)t * plane;
-        const uint32_t *Zt = P.Z + (size_t)(t * 2) * (size_t)P.Y * twoK;
+        // wait for prime t's group (groups complete in order)
+        switch (r - 1 - t) {
+            case 0: cp_async_wait<0>(); break;
+            case 1: cp_async_wait<1>(); break;
+            case 2: cp_async_wait<2>(); break;
+            case 3: cp_async_wait<3>(); break;
+            case 4: cp_async_wait<4>(); break;
+            default: cp_async_wait<5>(); break;
+        }
+        __syncthreads();
         for (int e = threadIdx.x; e < Y2 * twoK; e += blockDim.x) {
             const int pos = e >> (logK + 1), col = e & (twoK - 1);
             const uint32_t k2 = bitrev((uint32_t)pos, P.logY2);
-            const uint32_t v = Zt[((size_t)pos * Y1 + i1) * twoK + col];
-            Rt[(size_t)pos * pitch + col] = shoup(v, __ldg(pc.ty_i + (size_t)i1 * k2), p);
+            uint32_t *x = Rt + (size_t)pos * pitch + col;
+            *x = shoup(*x, __ldg(pc.ty_i + (size_t)i1 * k2), p);
         }
         __syncthreads();
         const TileMap ym{Rt, twoK, twoK, 1, 0, pitch};

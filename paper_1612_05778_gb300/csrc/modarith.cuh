@@ -51,113 +51,18 @@ __device__ __forceinline__ void bf_dit(uint32_t &x, uint32_t &y, uint2 w, uint32
     y = d;
 }
 
-// ---------------------------------------------------------------------------
-// Radix-2 stages over a shared-memory tile.  A twiddle table of order
-// T = 2^logT holds (omega_T^e, Shoup quotient); a stage of half-size h uses
-// omega_{2h}^k = omega_T^{k T / (2h)}.
-// ---------------------------------------------------------------------------
-
-// nt transforms of length 2^logL along contiguous elements; transform i
-// starts at s + i*tstride.  Forward (DIF): natural order in, bit-reversed out.
-__device__ __forceinline__ void dif_rows(uint32_t *s, int nt, int tstride, int logL,
-                                         const uint2 *__restrict__ tw, int logT, uint32_t p,
-                                         uint32_t p2) {
-    if (logL == 0) return;
-    const int halfm = (1 << (logL - 1)) - 1;
-    const int total = nt << (logL - 1);
-    for (int logh = logL - 1; logh >= 0; --logh) {
-        const int h = 1 << logh;
-        for (int b = threadIdx.x; b < total; b += blockDim.x) {
-            const int tr = b >> (logL - 1);
-            const int k = b & halfm;
-            const int kk = k & (h - 1);
-            const int i0 = ((k >> logh) << (logh + 1)) + kk;
-            uint32_t *x = s + tr * tstride;
-            const uint2 w = tw[kk << (logT - logh - 1)];
-            uint32_t u = x[i0], v = x[i0 + h];
-            bf_dif(u, v, w, p, p2);
-            x[i0] = u;
-            x[i0 + h] = v;
-        }
-        __syncthreads();
-    }
+// Asynchronous 4-byte global -> shared copies (LDGSTS, sm_80+): the data
+// land in shared memory without passing through registers, so a thread can
+// issue a whole tile's loads and work on other data while they fly.
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
-
-// Inverse (DIT): bit-reversed order in, natural order out (unnormalised).
-__device__ __forceinline__ void dit_rows(uint32_t *s, int nt, int tstride, int logL,
-                                         const uint2 *__restrict__ tw, int logT, uint32_t p,
-                                         uint32_t p2) {
-    if (logL == 0) return;
-    const int halfm = (1 << (logL - 1)) - 1;
-    const int total = nt << (logL - 1);
-    for (int logh = 0; logh < logL; ++logh) {
-        const int h = 1 << logh;
-        for (int b = threadIdx.x; b < total; b += blockDim.x) {
-            const int tr = b >> (logL - 1);
-            const int k = b & halfm;
-            const int kk = k & (h - 1);
-            const int i0 = ((k >> logh) << (logh + 1)) + kk;
-            uint32_t *x = s + tr * tstride;
-            const uint2 w = tw[kk << (logT - logh - 1)];
-            uint32_t u = x[i0], v = x[i0 + h];
-            bf_dit(u, v, w, p, p2);
-            x[i0] = u;
-            x[i0 + h] = v;
-        }
-        __syncthreads();
-    }
-}
-
-// 2^logC columns of length 2^logL; column c is s[c + i*pitch], i < 2^logL.
-// Consecutive threads take consecutive columns (conflict-free rows).
-__device__ __forceinline__ void dif_cols(uint32_t *s, int logC, int pitch, int logL,
-                                         const uint2 *__restrict__ tw, int logT, uint32_t p,
-                                         uint32_t p2) {
-    if (logL == 0) return;
-    const int cm = (1 << logC) - 1;
-    const int total = 1 << (logC + logL - 1);
-    for (int logh = logL - 1; logh >= 0; --logh) {
-        const int h = 1 << logh;
-        for (int b = threadIdx.x; b < total; b += blockDim.x) {
-            const int c = b & cm;
-            const int k = b >> logC;
-            const int kk = k & (h - 1);
-            const int i0 = ((k >> logh) << (logh + 1)) + kk;
-            const uint2 w = tw[kk << (logT - logh - 1)];
-            uint32_t *x0 = s + c + i0 * pitch;
-            uint32_t *x1 = x0 + h * pitch;
-            uint32_t u = *x0, v = *x1;
-            bf_dif(u, v, w, p, p2);
-            *x0 = u;
-            *x1 = v;
-        }
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ void dit_cols(uint32_t *s, int logC, int pitch, int logL,
-                                         const uint2 *__restrict__ tw, int logT, uint32_t p,
-                                         uint32_t p2) {
-    if (logL == 0) return;
-    const int cm = (1 << logC) - 1;
-    const int total = 1 << (logC + logL - 1);
-    for (int logh = 0; logh < logL; ++logh) {
-        const int h = 1 << logh;
-        for (int b = threadIdx.x; b < total; b += blockDim.x) {
-            const int c = b & cm;
-            const int k = b >> logC;
-            const int kk = k & (h - 1);
-            const int i0 = ((k >> logh) << (logh + 1)) + kk;
-            const uint2 w = tw[kk << (logT - logh - 1)];
-            uint32_t *x0 = s + c + i0 * pitch;
-            uint32_t *x1 = x0 + h * pitch;
-            uint32_t u = *x0, v = *x1;
-            bf_dit(u, v, w, p, p2);
-            *x0 = u;
-            *x1 = v;
-        }
-        __syncthreads();
-    }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Wait until at most N of this thread's committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits) {
