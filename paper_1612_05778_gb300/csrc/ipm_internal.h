@@ -13,10 +13,14 @@ constexpr int PRIME_ORDER_LOG2 = 21; // every prime p satisfies 2^21 | p - 1
 constexpr int KMAX_LOG2 = 11;        // K <= 2048 digits per coefficient
 constexpr int MMAX = 62;             // digit width, |digit| <= 2^(M-1) < 2^63
 
-// Tile budgets (bytes of dynamic shared memory).
-constexpr size_t SMEM_FWD_MAX = 100 * 1024;
-constexpr size_t SMEM_INV_MAX = 112 * 1024;
-constexpr size_t SMEM_MID_MAX = 200 * 1024;
+// Dynamic shared memory: hard limit per block (sm_103a allows 227 KB), and
+// the sizes below which 3 forward / 2 inverse CTAs fit on one SM.
+constexpr size_t SMEM_BLOCK_MAX = 227 * 1024;
+constexpr size_t SMEM_FWD_MAX = SMEM_BLOCK_MAX;
+constexpr size_t SMEM_INV_MAX = SMEM_BLOCK_MAX;
+constexpr size_t SMEM_MID_MAX = SMEM_BLOCK_MAX;
+constexpr size_t SMEM_FWD_3PERSM = 74 * 1024;
+constexpr size_t SMEM_INV_2PERSM = 112 * 1024;
 
 constexpr int THREADS_FWD = 256;
 constexpr int THREADS_MID = 1024;
@@ -54,6 +58,7 @@ struct KParams {
     int32_t K, logK, M, N, r;
     int64_t Y, Y1, Y2;
     int32_t logY, logY1, logY2, S, logS;
+    int32_t mid_tables_in_smem;  // middle pass keeps its omega_Y1 tables in shared memory
     PrimeConst pc[RMAX];
     // Garner: ginv[t][s] = p_s^{-1} mod p_t (s < t), with Shoup quotients.
     uint32_t ginv[RMAX][RMAX];

@@ -182,6 +182,12 @@ k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a,
 // Pass 2
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ const uint2 *pc_tables_f(const KParams &P, int t) { return P.pc[t].t1_f; }
+__device__ __forceinline__ const uint2 *pc_tables_i(const KParams &P, int t) { return P.pc[t].t1_i; }
+
+// SMTW: the omega_Y1 tables are copied to shared memory (else read from
+// global memory through the non-coherent cache).
+template <bool SMTW>
 __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant__ KParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int cs = blockIdx.x, pos = blockIdx.y, t = blockIdx.z;
@@ -189,9 +195,11 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
     const int pitch = S + 1;  // odd pitch for conflict-free strided gathers
     const int twoK = 2 * P.K;
     const int Y1 = (int)P.Y1;
-    uint2 *twf = reinterpret_cast<uint2 *>(smem);       // omega_Y1^e, e < Y1
-    uint2 *twi = twf + Y1;                              // omega_Y1^{-e}
-    uint32_t *A = reinterpret_cast<uint32_t *>(twi + Y1);  // [Y1][pitch]
+    uint2 *twf_s = reinterpret_cast<uint2 *>(smem);     // omega_Y1^e, e < Y1
+    uint2 *twi_s = twf_s + Y1;                          // omega_Y1^{-e}
+    const uint2 *twf = SMTW ? twf_s : pc_tables_f(P, blockIdx.z);
+    const uint2 *twi = SMTW ? twi_s : pc_tables_i(P, blockIdx.z);
+    uint32_t *A = reinterpret_cast<uint32_t *>(SMTW ? (void *)(twi_s + Y1) : (void *)smem);  // [Y1][pitch]
     uint32_t *B = A + (size_t)Y1 * pitch + 16;          // [Y1][pitch], shifted 16 banks
     const PrimeConst &pc = P.pc[t];
     const uint32_t p = pc.p, p2 = pc.p2;
@@ -210,19 +218,21 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
         cp_async4(B + i1 * pitch + c, ZB + base + (size_t)i1 * twoK + c);
     }
     cp_async_commit();
-    for (int e = threadIdx.x; e < Y1; e += blockDim.x) {
-        twf[e] = __ldg(pc.t1_f + e);
-        twi[e] = __ldg(pc.t1_i + e);
+    if (SMTW) {
+        for (int e = threadIdx.x; e < Y1; e += blockDim.x) {
+            twf_s[e] = __ldg(pc.t1_f + e);
+            twi_s[e] = __ldg(pc.t1_i + e);
+        }
     }
     cp_async_wait<1>();
     __syncthreads();
     // y step C (omega_Y1 = omega_Y^Y2) on the S columns of A, then of B
     const TileMap am{A, S, S, 1, 0, pitch};
-    ntt_forward<true>(am, P.logY1, twf, P.logY1, p, p2);
+    ntt_forward<SMTW>(am, P.logY1, twf, P.logY1, p, p2);
     cp_async_wait<0>();
     __syncthreads();
     const TileMap bm{B, S, S, 1, 0, pitch};
-    ntt_forward<true>(bm, P.logY1, twf, P.logY1, p, p2);
+    ntt_forward<SMTW>(bm, P.logY1, twf, P.logY1, p, p2);
     // pointwise product in Montgomery form: A*B*2^-32 (the 2^32 is put back
     // by the scale factor of the inverse pass)
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
@@ -230,7 +240,7 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
         A[i] = montmul(A[i], B[i], p, pc.mont);
     }
     __syncthreads();
-    ntt_inverse<true>(am, P.logY1, twi, P.logY1, p, p2);
+    ntt_inverse<SMTW>(am, P.logY1, twi, P.logY1, p, p2);
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
         const int i1 = e >> logS, c = e & (S - 1);
         ZA[base + (size_t)i1 * twoK + c] = red(A[i1 * pitch + c], p);
@@ -561,8 +571,11 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
 int set_kernel_attributes() {
     cudaError_t e1 = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)SMEM_FWD_MAX);
-    cudaError_t e2 = cudaFuncSetAttribute(k_middle, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e2 = cudaFuncSetAttribute(k_middle<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)SMEM_MID_MAX);
+    if (e2 == cudaSuccess)
+        e2 = cudaFuncSetAttribute(k_middle<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SMEM_MID_MAX);
     cudaError_t e3 = cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)SMEM_INV_MAX);
     return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) ? 0 : -1;
@@ -578,7 +591,10 @@ int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint
 
 int launch_middle(const KParams &kp, size_t smem, void *stream) {
     dim3 grid((unsigned)(2 * kp.K / kp.S), (unsigned)kp.Y2, (unsigned)kp.r);
-    k_middle<<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
+    if (kp.mid_tables_in_smem)
+        k_middle<true><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
+    else
+        k_middle<false><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
     g_launches.fetch_add(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -148,6 +148,7 @@ int big_cmp(const Big &a, const Big &b) {
 struct Tiles {
     int64_t Y2;
     int32_t S;
+    bool mid_tables;
     size_t smem_fwd, smem_mid, smem_inv;
 };
 
@@ -156,41 +157,58 @@ size_t inv_smem(int64_t Y2, int K, int r, int lc) {
     size_t sources = ((size_t)lc + 1) * 16;  // one uint4 per limb
     return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources;
 }
-size_t mid_smem(int64_t Y1, int S) { return ((size_t)2 * Y1 * (S + 1) + 16) * 4 + (size_t)2 * Y1 * 8; }
+size_t mid_smem(int64_t Y1, int S, bool tables) {
+    return ((size_t)2 * Y1 * (S + 1) + 16) * 4 + (tables ? (size_t)2 * Y1 * 8 : 0);
+}
 
-// Tile shapes: Y2 rows per forward/inverse tile, S columns per middle tile.
+// Tile shapes: Y2 rows per forward/inverse tile, S columns per middle tile
+// (Y1 = Y / Y2 is the middle pass's column length).  Hard limit: every pass
+// fits one block's shared memory.  Preferences, in order: middle slices of
+// at least 8 columns (32-byte DRAM sectors), an inverse tile small enough
+// for two CTAs per SM, a forward tile small enough for three, and Y2 close
+// to max(32, Y / 2048) (the middle pass's twiddle tables stay small).
 bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force, Tiles &t) {
-    int64_t y2max = 1;
-    for (int64_t y2 = std::min<int64_t>(Y, 256); y2 >= 1; y2 >>= 1) {
-        if (fwd_smem(y2, K) <= SMEM_FWD_MAX && inv_smem(y2, K, r, lc) <= SMEM_INV_MAX) {
-            y2max = y2;
-            break;
+    const int64_t target = std::max<int64_t>(std::min<int64_t>(32, Y), Y / 2048);
+    bool found = false;
+    double best = 0;
+    for (int64_t Y2 = 1; Y2 <= Y && Y2 <= 8192; Y2 <<= 1) {
+        if (y2_force && Y2 != y2_force) continue;
+        const size_t fw = fwd_smem(Y2, K), iv = inv_smem(Y2, K, r, lc);
+        if (fw > SMEM_FWD_MAX || iv > SMEM_INV_MAX) continue;
+        const int64_t Y1 = Y / Y2;
+        // widest slice that fits, with the twiddle tables in shared memory
+        // if possible, else read from global memory
+        int S = 0;
+        bool tab = true;
+        for (int pass = 0; pass < 2 && S == 0; ++pass) {
+            tab = pass == 0;
+            for (int s = std::min(2 * K, 32); s >= 1; s >>= 1) {
+                if (s_force && s != s_force) continue;
+                if (mid_smem(Y1, s, tab) <= SMEM_MID_MAX) { S = s; break; }
+            }
+            if (tab && S > 0 && S < 8 && S < 2 * K && !s_force) {
+                // a wider slice without the tables beats a narrow one with them
+                for (int s = std::min(2 * K, 32); s > S; s >>= 1)
+                    if (mid_smem(Y1, s, false) <= SMEM_MID_MAX) { S = s; tab = false; break; }
+            }
         }
-        if (y2 == 1) return false;
+        if (s_force && (s_force > 2 * K || (s_force & (s_force - 1)))) S = 0;
+        if (S == 0) continue;
+        double score = (S >= 8 || S == 2 * K ? 0 : 8) + (iv <= SMEM_INV_2PERSM ? 0 : 4) +
+                       (fw <= SMEM_FWD_3PERSM ? 0 : 2) + (tab ? 0 : 1) +
+                       0.1 * std::abs(ilog2((uint64_t)Y2) - ilog2((uint64_t)target));
+        if (!found || score < best) {
+            found = true;
+            best = score;
+            t.Y2 = Y2;
+            t.S = S;
+            t.mid_tables = tab;
+            t.smem_fwd = fw;
+            t.smem_mid = mid_smem(Y1, S, tab);
+            t.smem_inv = iv;
+        }
     }
-    int64_t Y2 = std::min<int64_t>(y2max, std::max<int64_t>(1, Y / 64));
-    if (y2_force) {
-        if (y2_force > Y || (y2_force & (y2_force - 1)) || fwd_smem(y2_force, K) > SMEM_FWD_MAX ||
-            inv_smem(y2_force, K, r, lc) > SMEM_INV_MAX)
-            return false;
-        Y2 = y2_force;
-    }
-    int64_t Y1 = Y / Y2;
-    int S = 0;
-    for (int s = std::min(2 * K, 32); s >= 1; s >>= 1)
-        if (mid_smem(Y1, s) <= SMEM_MID_MAX) { S = s; break; }
-    if (s_force) {
-        if (s_force > 2 * K || (s_force & (s_force - 1)) || mid_smem(Y1, s_force) > SMEM_MID_MAX)
-            return false;
-        S = s_force;
-    }
-    if (S == 0) return false;
-    t.Y2 = Y2;
-    t.S = S;
-    t.smem_fwd = fwd_smem(Y2, K);
-    t.smem_mid = mid_smem(Y1, S);
-    t.smem_inv = inv_smem(Y2, K, r, lc);
-    return true;
+    return found;
 }
 
 }  // namespace
@@ -290,6 +308,7 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
         kp.Y = Y; kp.Y2 = tl.Y2; kp.Y1 = Y / tl.Y2;
         kp.logY = logY; kp.logY2 = ilog2((uint64_t)tl.Y2); kp.logY1 = logY - kp.logY2;
         kp.S = tl.S; kp.logS = ilog2((uint64_t)tl.S);
+        kp.mid_tables_in_smem = tl.mid_tables ? 1 : 0;
         best = s;
     }
     if (!found) return (P.K || P.M || P.r || P.y2 || P.s) ? IPM_ERR_ARG : IPM_ERR_UNSUPPORTED;

@@ -243,3 +243,28 @@ def test_large_all_ones_closed_form():
     n = sh.na
     bad = [k for k in range(sh.nc) if C[k] != terms(k, n, n) * alpha2]
     assert not bad, bad[:10]
+
+
+def _sampled_and_identities(sh, a, b, extra_ks=()):
+    got, info = gpu_mul(a, b, sh.bits_a, sh.bits_b)
+    assert info["lc"] == sh.lc
+    nc = sh.nc
+    ks = [0, 1, 2, 1000, nc // 4, nc // 2 - 1, nc // 2, nc // 2 + 1, nc - 2, nc - 1, *extra_ks]
+    ks += np.random.default_rng(nc).integers(0, nc, 4).tolist()
+    want = oracle.coeffs(ks, a, b, sh.lc)
+    assert_same((got[0][ks], got[1][ks]), want)
+    _whole_output_identities(a, b, got)
+    return info
+
+
+def test_huge_dense_full_size():
+    """Two degree-262143 polynomials, 1024-bit coefficients (seed 2)."""
+    sh, a, b = W.huge_dense(seed=2)
+    info = _sampled_and_identities(sh, a, b)
+    assert info["Y"] == 1 << 19
+
+
+def test_huge_mixed_full_size():
+    """Half the positions < 2^64, the rest < 2^2048, random positions."""
+    sh, a, b = W.huge_mixed(seed=2)
+    _sampled_and_identities(sh, a, b)
