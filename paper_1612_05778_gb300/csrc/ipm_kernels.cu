@@ -43,7 +43,10 @@ __device__ __forceinline__ uint32_t twos_limb(const uint32_t *row, int L, bool n
     return l == f ? 0u - v : ~v;
 }
 
-__global__ void __launch_bounds__(THREADS_FWD, 3)
+// NT threads per block: THREADS_FWD (three blocks per SM) for tiles that
+// leave room for three, 1024 (one block) for tiles that fill an SM.
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == THREADS_FWD ? 3 : 1)
 k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a,
           const uint8_t *__restrict__ an, const uint32_t *__restrict__ b,
           const uint8_t *__restrict__ bn) {
@@ -469,7 +472,9 @@ __device__ __forceinline__ void recombine_rows(const KParams &P, const uint32_t 
     }
 }
 
-__global__ void __launch_bounds__(THREADS_INV, 2)
+// NT threads per block: THREADS_INV (two blocks per SM) or 1024 (one).
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == THREADS_INV ? 2 : 1)
 k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *__restrict__ cn) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t i1 = blockIdx.x;
@@ -569,22 +574,26 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
 // ---------------------------------------------------------------------------
 
 int set_kernel_attributes() {
-    cudaError_t e1 = cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)SMEM_FWD_MAX);
-    cudaError_t e2 = cudaFuncSetAttribute(k_middle<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)SMEM_MID_MAX);
-    if (e2 == cudaSuccess)
-        e2 = cudaFuncSetAttribute(k_middle<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SMEM_MID_MAX);
-    cudaError_t e3 = cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)SMEM_INV_MAX);
-    return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) ? 0 : -1;
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *f, size_t bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    set((const void *)k_forward<THREADS_FWD>, SMEM_FWD_MAX);
+    set((const void *)k_forward<1024>, SMEM_FWD_MAX);
+    set((const void *)k_middle<true>, SMEM_MID_MAX);
+    set((const void *)k_middle<false>, SMEM_MID_MAX);
+    set((const void *)k_inverse<THREADS_INV>, SMEM_INV_MAX);
+    set((const void *)k_inverse<1024>, SMEM_INV_MAX);
+    return e == cudaSuccess ? 0 : -1;
 }
 
 int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint8_t *an,
                    const uint32_t *b, const uint8_t *bn, void *stream) {
     dim3 grid((unsigned)kp.Y1, 2, 1);
-    k_forward<<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
+    if (smem <= SMEM_FWD_3PERSM)
+        k_forward<THREADS_FWD><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
+    else
+        k_forward<1024><<<grid, 1024, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
     g_launches.fetch_add(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -601,7 +610,10 @@ int launch_middle(const KParams &kp, size_t smem, void *stream) {
 
 int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, void *stream) {
     dim3 grid((unsigned)kp.Y1, 1, 1);
-    k_inverse<<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
+    if (smem <= SMEM_INV_2PERSM)
+        k_inverse<THREADS_INV><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
+    else
+        k_inverse<1024><<<grid, 1024, smem, (cudaStream_t)stream>>>(kp, c, cn);
     g_launches.fetch_add(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
