@@ -152,9 +152,11 @@ typedef struct {
 
 /*
  * n independent products ops[i] with shapes[i] of the plan (n must equal
- * the plan's shape count).  `ops` is a HOST array of device pointers.
- * Products run one after another on `stream` (§2.4 parallelises within a
- * product; so does every kernel here).
+ * the plan's shape count).  `ops` is a HOST array of device pointers; it may
+ * be reused as soon as the call returns.  The plan groups its shapes by
+ * kernel variant (at most 4 GiB of workspace per group) and runs each
+ * group's products together: three launches per group, every block finding
+ * its product and tile in device tables built by ipm_plan.
  */
 ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n,
                            ipm_stream_t stream);

@@ -1,6 +1,7 @@
 // ipm_api.cu -- the C ABI of include/ipm.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <new>
@@ -21,6 +22,9 @@ struct ipm_plan_s {
     // ipm_mul_host staging (allocated on first use)
     unsigned char *io = nullptr;
     size_t io_bytes = 0;
+    // batched calls (n > 1): groups of products launched together
+    std::vector<BatchLaunch> batch;
+    ipm_operands *d_ops = nullptr;    // operand pointers of the current call
     // per-pass profiling events (ipm_set_profiling)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool profiling = false;
@@ -73,6 +77,118 @@ ipm_status read_error(ipm_plan_s *plan, void *stream) {
         if (e != cudaSuccess) return cuda_status(e);
         if (h & ERRBIT_BOUND) return IPM_ERR_BOUND;
         return IPM_ERR_CUDA;
+    }
+    return IPM_OK;
+}
+
+
+// ---- batched schedule ------------------------------------------------------
+
+// Products of one batched group run concurrently, each in its own slice of
+// the workspace; a group is closed when the next product would take the
+// group's workspace past this size (4 GiB), so memory stays bounded.
+constexpr size_t kBatchWorkspaceWords = (size_t)1 << 30;
+
+struct VariantKey {
+    bool fwd_small, mid_tables, inv_small;
+    bool operator<(const VariantKey &o) const {
+        return std::tie(fwd_small, mid_tables, inv_small) < std::tie(o.fwd_small, o.mid_tables, o.inv_small);
+    }
+};
+
+VariantKey variant_of(const ShapePlan &sp) {
+    return VariantKey{sp.smem_fwd <= SMEM_FWD_3PERSM, sp.kp.mid_tables_in_smem != 0,
+                      sp.smem_inv <= SMEM_INV_2PERSM};
+}
+
+// Groups of shape indices: same kernel variants, bounded workspace,
+// largest products first (they bound the group's run time).
+std::vector<std::vector<int>> batch_groups(const std::vector<ShapePlan> &shapes) {
+    std::map<VariantKey, std::vector<int>> by_variant;
+    for (int i = 0; i < (int)shapes.size(); ++i) by_variant[variant_of(shapes[(size_t)i])].push_back(i);
+    std::vector<std::vector<int>> groups;
+    for (auto &kv : by_variant) {
+        auto &v = kv.second;
+        std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
+            return shapes[(size_t)x].z_words > shapes[(size_t)y].z_words;
+        });
+        std::vector<int> cur;
+        size_t words = 0;
+        for (int i : v) {
+            const size_t z = shapes[(size_t)i].z_words;
+            if (!cur.empty() && words + z > kBatchWorkspaceWords) {
+                groups.push_back(cur);
+                cur.clear();
+                words = 0;
+            }
+            cur.push_back(i);
+            words += z;
+        }
+        if (!cur.empty()) groups.push_back(cur);
+    }
+    return groups;
+}
+
+size_t batch_workspace_words(const std::vector<ShapePlan> &shapes) {
+    size_t most = 0;
+    for (const auto &g : batch_groups(shapes)) {
+        size_t w = 0;
+        for (int i : g) w += (shapes[(size_t)i].z_words + 63) & ~(size_t)63;
+        most = std::max(most, w);
+    }
+    return most;
+}
+
+ipm_status build_batch(ipm_plan_s *plan) {
+    const auto &shapes = plan->shapes;
+    cudaError_t ce;
+    void *d = nullptr;
+    ce = cudaMalloc(&d, shapes.size() * sizeof(ipm_operands));
+    if (ce != cudaSuccess) return cuda_status(ce);
+    plan->allocations.push_back(d);
+    plan->d_ops = (ipm_operands *)d;
+    for (const auto &g : batch_groups(shapes)) {
+        std::vector<KParams> params;
+        std::vector<uint2> items[3];
+        BatchLaunch bl{};
+        const VariantKey vk = variant_of(shapes[(size_t)g[0]]);
+        bl.fwd_small = vk.fwd_small;
+        bl.mid_tables = vk.mid_tables;
+        bl.inv_small = vk.inv_small;
+        size_t zoff = 0;
+        for (int i : g) {
+            const ShapePlan &sp = shapes[(size_t)i];
+            KParams kp = sp.kp;
+            kp.Z = plan->Z + zoff;
+            kp.batch_index = i;
+            zoff += (sp.z_words + 63) & ~(size_t)63;
+            const uint32_t pi = (uint32_t)params.size();
+            params.push_back(kp);
+            for (uint32_t t = 0; t < (uint32_t)(2 * kp.Y1); ++t) items[0].push_back(make_uint2(pi, t));
+            const uint32_t nmid = (uint32_t)((2 * kp.K / kp.S) * kp.Y2 * kp.r);
+            for (uint32_t t = 0; t < nmid; ++t) items[1].push_back(make_uint2(pi, t));
+            for (uint32_t t = 0; t < (uint32_t)kp.Y1; ++t) items[2].push_back(make_uint2(pi, t));
+            bl.smem[0] = std::max(bl.smem[0], sp.smem_fwd);
+            bl.smem[1] = std::max(bl.smem[1], sp.smem_mid);
+            bl.smem[2] = std::max(bl.smem[2], sp.smem_inv);
+        }
+        ce = cudaMalloc(&d, params.size() * sizeof(KParams));
+        if (ce != cudaSuccess) return cuda_status(ce);
+        plan->allocations.push_back(d);
+        if ((ce = cudaMemcpy(d, params.data(), params.size() * sizeof(KParams), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_status(ce);
+        bl.params = (const KParams *)d;
+        for (int p = 0; p < 3; ++p) {
+            ce = cudaMalloc(&d, items[p].size() * sizeof(uint2));
+            if (ce != cudaSuccess) return cuda_status(ce);
+            plan->allocations.push_back(d);
+            if ((ce = cudaMemcpy(d, items[p].data(), items[p].size() * sizeof(uint2), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+                return cuda_status(ce);
+            bl.items[p] = (const uint2 *)d;
+            bl.nitems[p] = (unsigned)items[p].size();
+        }
+        plan->batch.push_back(bl);
     }
     return IPM_OK;
 }
@@ -134,6 +250,9 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
             sp.kp.pc[t].untw = blk + L.untw;
         }
     }
+    // batched calls run a group's products at once: the workspace holds the
+    // largest group (groups are cut at kBatchWorkspaceWords or one product)
+    if (n > 1) zmax = std::max(zmax, batch_workspace_words(plan->shapes));
     void *d = nullptr;
     ce = cudaMalloc(&d, zmax * sizeof(uint32_t));
     if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
@@ -148,6 +267,10 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
     for (auto &sp : plan->shapes) {
         sp.kp.Z = plan->Z;
         sp.kp.err = plan->err;
+    }
+    if (n > 1) {
+        ipm_status st = build_batch(plan);
+        if (st != IPM_OK) { free_plan(plan); return st; }
     }
     *out = plan;
     return IPM_OK;
@@ -205,11 +328,24 @@ ipm_status ipm_mul_host(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg
 }
 
 ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n, ipm_stream_t stream) {
-    if (!plan || !ops || n < 0 || (size_t)n != plan->shapes.size()) return IPM_ERR_ARG;
+    if (!plan || !ops || n < 1 || (size_t)n != plan->shapes.size()) return IPM_ERR_ARG;
     for (int32_t i = 0; i < n; ++i) {
         const ipm_operands &o = ops[i];
-        ipm_status st = run_one(plan, plan->shapes[(size_t)i], o.a, o.a_neg, o.b, o.b_neg, o.c, o.c_neg, stream);
+        if (!o.a || !o.a_neg || !o.b || !o.b_neg || !o.c || !o.c_neg) return IPM_ERR_ARG;
+        if (!aligned16(o.a) || !aligned16(o.b) || !aligned16(o.c)) return IPM_ERR_ARG;
+    }
+    if (n == 1) {
+        const ipm_operands &o = ops[0];
+        ipm_status st = run_one(plan, plan->shapes[0], o.a, o.a_neg, o.b, o.b_neg, o.c, o.c_neg, stream);
         if (st != IPM_OK) return st;
+    } else {
+        // operand pointers to the device (a pageable copy: the host array may
+        // be reused as soon as this call returns)
+        cudaError_t ce = cudaMemcpyAsync(plan->d_ops, ops, (size_t)n * sizeof(ipm_operands),
+                                         cudaMemcpyHostToDevice, (cudaStream_t)stream);
+        if (ce != cudaSuccess) return cuda_status(ce);
+        for (const auto &bl : plan->batch)
+            if (launch_batch(bl, plan->d_ops, stream)) return IPM_ERR_CUDA;
     }
     if (plan->flags & IPM_SYNC) return read_error(plan, stream);
     return IPM_OK;

@@ -67,6 +67,7 @@ struct KParams {
     uint32_t m_words[RMAX];
     uint32_t *Z;          // workspace: r x 2 x Y x 2K words
     int *err;             // device error word
+    int32_t batch_index;  // batched launches: index of this product's operands
 };
 
 // Host-side plan record for one shape.
@@ -97,6 +98,17 @@ int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint
 int launch_middle(const KParams &kp, size_t smem, void *stream);
 int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, void *stream);
 int set_kernel_attributes();
+
+// One group of a batched call: products that share the kernel variants,
+// launched as three ragged grids.  items[p][b] = (index into params, tile).
+struct BatchLaunch {
+    const KParams *params;    // device array
+    const uint2 *items[3];    // device arrays, one per pass
+    unsigned nitems[3];
+    size_t smem[3];           // largest tile of the group, per pass
+    bool fwd_small, mid_tables, inv_small;
+};
+int launch_batch(const BatchLaunch &bl, const ipm_operands *ops, void *stream);
 int64_t launches_so_far();
 
 }  // namespace ipm

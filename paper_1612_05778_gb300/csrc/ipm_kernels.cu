@@ -43,16 +43,11 @@ __device__ __forceinline__ uint32_t twos_limb(const uint32_t *row, int L, bool n
     return l == f ? 0u - v : ~v;
 }
 
-// NT threads per block: THREADS_FWD (three blocks per SM) for tiles that
-// leave room for three, 1024 (one block) for tiles that fill an SM.
-template <int NT>
-__global__ void __launch_bounds__(NT, NT == THREADS_FWD ? 3 : 1)
-k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a,
-          const uint8_t *__restrict__ an, const uint32_t *__restrict__ b,
-          const uint8_t *__restrict__ bn) {
+// Pass 1 on one tile: rows i = i1 + Y1*i2 (i2 < Y2) of operand op.
+__device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
+                                         const uint32_t *__restrict__ a, const uint8_t *__restrict__ an,
+                                         const uint32_t *__restrict__ b, const uint8_t *__restrict__ bn) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int op = blockIdx.y;
-    const int64_t i1 = blockIdx.x;
     const uint32_t *X = op ? b : a;
     const uint8_t *Xn = op ? bn : an;
     const int64_t nX = op ? P.nb : P.na;
@@ -188,20 +183,20 @@ k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a,
 __device__ __forceinline__ const uint2 *pc_tables_f(const KParams &P, int t) { return P.pc[t].t1_f; }
 __device__ __forceinline__ const uint2 *pc_tables_i(const KParams &P, int t) { return P.pc[t].t1_i; }
 
-// SMTW: the omega_Y1 tables are copied to shared memory (else read from
-// global memory through the non-coherent cache).
+// Pass 2 on one tile: columns [cs S, cs S + S) of the rows (pos, i1), i1 < Y1,
+// prime t.  SMTW: the omega_Y1 tables are copied to shared memory (else read
+// from global memory through the non-coherent cache).
 template <bool SMTW>
-__global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant__ KParams P) {
+__device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int t) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int cs = blockIdx.x, pos = blockIdx.y, t = blockIdx.z;
     const int S = P.S, logS = P.logS;
     const int pitch = S + 1;  // odd pitch for conflict-free strided gathers
     const int twoK = 2 * P.K;
     const int Y1 = (int)P.Y1;
     uint2 *twf_s = reinterpret_cast<uint2 *>(smem);     // omega_Y1^e, e < Y1
     uint2 *twi_s = twf_s + Y1;                          // omega_Y1^{-e}
-    const uint2 *twf = SMTW ? twf_s : pc_tables_f(P, blockIdx.z);
-    const uint2 *twi = SMTW ? twi_s : pc_tables_i(P, blockIdx.z);
+    const uint2 *twf = SMTW ? twf_s : pc_tables_f(P, t);
+    const uint2 *twi = SMTW ? twi_s : pc_tables_i(P, t);
     uint32_t *A = reinterpret_cast<uint32_t *>(SMTW ? (void *)(twi_s + Y1) : (void *)smem);  // [Y1][pitch]
     uint32_t *B = A + (size_t)Y1 * pitch + 16;          // [Y1][pitch], shifted 16 banks
     const PrimeConst &pc = P.pc[t];
@@ -472,12 +467,10 @@ __device__ __forceinline__ void recombine_rows(const KParams &P, const uint32_t 
     }
 }
 
-// NT threads per block: THREADS_INV (two blocks per SM) or 1024 (one).
-template <int NT>
-__global__ void __launch_bounds__(NT, NT == THREADS_INV ? 2 : 1)
-k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *__restrict__ cn) {
+// Pass 3 on one tile: output rows i = i1 + Y1*i2 (i2 < Y2).
+__device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t *__restrict__ c,
+                                         uint8_t *__restrict__ cn) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t i1 = blockIdx.x;
     const int K = P.K, logK = P.logK, twoK = 2 * K, r = P.r, M = P.M;
     const int Y2 = (int)P.Y2;
     const int64_t Y1 = P.Y1;
@@ -570,6 +563,64 @@ k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *
 }
 
 // ---------------------------------------------------------------------------
+// Kernels.  Single product: the plan's constants are a __grid_constant__
+// parameter and the grid is the tile grid.  Batched: one launch covers the
+// tiles of many products; block b reads (product, tile) = items[b] and that
+// product's constants and operand pointers from device arrays.
+// Forward/inverse come in two block sizes: THREADS_FWD / THREADS_INV for
+// tiles that leave room for several blocks per SM, 1024 for tiles that fill
+// an SM.
+// ---------------------------------------------------------------------------
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == THREADS_FWD ? 3 : 1)
+k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a, const uint8_t *__restrict__ an,
+          const uint32_t *__restrict__ b, const uint8_t *__restrict__ bn) {
+    fwd_tile(P, blockIdx.x, blockIdx.y, a, an, b, bn);
+}
+
+template <bool SMTW>
+__global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant__ KParams P) {
+    mid_tile<SMTW>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == THREADS_INV ? 2 : 1)
+k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *__restrict__ cn) {
+    inv_tile(P, blockIdx.x, c, cn);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == THREADS_FWD ? 3 : 1)
+kb_forward(const KParams *__restrict__ Ps, const ipm_operands *__restrict__ ops, const uint2 *__restrict__ items) {
+    const uint2 it = items[blockIdx.x];
+    const KParams &P = Ps[it.x];
+    const ipm_operands o = ops[P.batch_index];
+    const int op = (int64_t)it.y >= P.Y1 ? 1 : 0;
+    fwd_tile(P, (int64_t)it.y - (op ? P.Y1 : 0), op, o.a, o.a_neg, o.b, o.b_neg);
+}
+
+template <bool SMTW>
+__global__ void __launch_bounds__(THREADS_MID, 1)
+kb_middle(const KParams *__restrict__ Ps, const uint2 *__restrict__ items) {
+    const uint2 it = items[blockIdx.x];
+    const KParams &P = Ps[it.x];
+    const int ncs = 2 * P.K / P.S;
+    const int cs = (int)(it.y % (uint32_t)ncs);
+    const int rest = (int)(it.y / (uint32_t)ncs);
+    mid_tile<SMTW>(P, cs, rest % (int)P.Y2, rest / (int)P.Y2);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == THREADS_INV ? 2 : 1)
+kb_inverse(const KParams *__restrict__ Ps, const ipm_operands *__restrict__ ops, const uint2 *__restrict__ items) {
+    const uint2 it = items[blockIdx.x];
+    const KParams &P = Ps[it.x];
+    const ipm_operands o = ops[P.batch_index];
+    inv_tile(P, it.y, o.c, o.c_neg);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 
@@ -584,7 +635,42 @@ int set_kernel_attributes() {
     set((const void *)k_middle<false>, SMEM_MID_MAX);
     set((const void *)k_inverse<THREADS_INV>, SMEM_INV_MAX);
     set((const void *)k_inverse<1024>, SMEM_INV_MAX);
+    set((const void *)kb_forward<THREADS_FWD>, SMEM_FWD_MAX);
+    set((const void *)kb_forward<1024>, SMEM_FWD_MAX);
+    set((const void *)kb_middle<true>, SMEM_MID_MAX);
+    set((const void *)kb_middle<false>, SMEM_MID_MAX);
+    set((const void *)kb_inverse<THREADS_INV>, SMEM_INV_MAX);
+    set((const void *)kb_inverse<1024>, SMEM_INV_MAX);
     return e == cudaSuccess ? 0 : -1;
+}
+
+int launch_batch(const BatchLaunch &bl, const ipm_operands *ops, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (bl.items[0]) {
+        if (bl.fwd_small)
+            kb_forward<THREADS_FWD><<<bl.nitems[0], THREADS_FWD, bl.smem[0], s>>>(bl.params, ops, bl.items[0]);
+        else
+            kb_forward<1024><<<bl.nitems[0], 1024, bl.smem[0], s>>>(bl.params, ops, bl.items[0]);
+        g_launches.fetch_add(1);
+        if (cudaGetLastError() != cudaSuccess) return -1;
+    }
+    if (bl.items[1]) {
+        if (bl.mid_tables)
+            kb_middle<true><<<bl.nitems[1], THREADS_MID, bl.smem[1], s>>>(bl.params, bl.items[1]);
+        else
+            kb_middle<false><<<bl.nitems[1], THREADS_MID, bl.smem[1], s>>>(bl.params, bl.items[1]);
+        g_launches.fetch_add(1);
+        if (cudaGetLastError() != cudaSuccess) return -1;
+    }
+    if (bl.items[2]) {
+        if (bl.inv_small)
+            kb_inverse<THREADS_INV><<<bl.nitems[2], THREADS_INV, bl.smem[2], s>>>(bl.params, ops, bl.items[2]);
+        else
+            kb_inverse<1024><<<bl.nitems[2], 1024, bl.smem[2], s>>>(bl.params, ops, bl.items[2]);
+        g_launches.fetch_add(1);
+        if (cudaGetLastError() != cudaSuccess) return -1;
+    }
+    return 0;
 }
 
 int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint8_t *an,
