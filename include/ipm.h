@@ -123,7 +123,7 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
 ipm_status ipm_get_info(ipm_plan_t plan, int32_t index, ipm_plan_info *out);
 
 /*
- * c = a*b (§2.3, lines 1-8 of the main algorithm) for a plan with n = 1.
+ * c = a*b (§2.3, the main algorithm) for a plan with n = 1.
  * a, a_neg, b, b_neg, c, c_neg are DEVICE pointers in the format above,
  * 16-byte aligned for the limb arrays.  c must not overlap a or b.
  */
