@@ -34,15 +34,6 @@ int64_t launches_so_far() { return g_launches.load(); }
 // Pass 1
 // ---------------------------------------------------------------------------
 
-// Limb l of the N-bit two's complement of a sign-magnitude coefficient
-// (row: L magnitude limbs; f: index of its lowest non-zero limb).
-__device__ __forceinline__ uint32_t twos_limb(const uint32_t *row, int L, bool neg, int f, int l) {
-    const uint32_t v = l < L ? row[l] : 0u;
-    if (!neg) return v;
-    if (l < f) return 0u;
-    return l == f ? 0u - v : ~v;
-}
-
 // Pass 1 on one tile: rows i = i1 + Y1*i2 (i2 < Y2) of operand op.
 __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
                                          const uint32_t *__restrict__ a, const uint8_t *__restrict__ an,
@@ -58,7 +49,10 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
     const int twoK = 2 * K;
     const int pitch = twoK + 1;  // odd row pitch: column walks hit distinct banks
     int64_t *dig = reinterpret_cast<int64_t *>(smem);            // [Y2][K]
-    uint32_t *tile = reinterpret_cast<uint32_t *>(dig + (size_t)Y2 * K);  // [Y2][pitch]
+    uint2 *tw_twist = reinterpret_cast<uint2 *>(dig + (size_t)Y2 * K);  // theta^j, j < K
+    uint2 *tw_rows = tw_twist + K;                               // omega_Y^{i1 k2(pos)}, pos < Y2
+    uint8_t *signs = reinterpret_cast<uint8_t *>(tw_rows + Y2);  // sign of row i2
+    uint32_t *tile = reinterpret_cast<uint32_t *>(signs + ((Y2 + 15) & ~15));  // [Y2][pitch]
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint64_t mmask = (1ull << M) - 1;
@@ -81,6 +75,7 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         const int i2 = e / L, l = e - i2 * L;
         tile[(size_t)i2 * pitch + l] = __ldg(X + (size_t)(i1 + Y1 * i2) * L + l);
     }
+    for (int i2 = threadIdx.x; i2 < nr; i2 += blockDim.x) signs[i2] = Xn[i1 + Y1 * i2];
     __syncthreads();
     for (int i2 = warp; i2 < Y2; i2 += nw) {
         const int64_t i = i1 + Y1 * (int64_t)i2;
@@ -89,7 +84,7 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
             for (int j = lane; j < K; j += 32) drow[j] = 0;
             continue;
         }
-        const uint32_t *row = tile + (size_t)i2 * pitch;
+        uint32_t *row = tile + (size_t)i2 * pitch;
         int f = L;
         for (int c0 = 0; c0 < L; c0 += 32) {
             const int l = c0 + lane;
@@ -99,7 +94,16 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         }
         if (lane == 0 && (bits & 31u) && (row[L - 1] >> (bits & 31u)))
             atomicOr(P.err, ERRBIT_BOUND);
-        const bool neg = Xn[i] != 0 && f < L;
+        const bool neg = signs[i2] != 0 && f < L;
+        // N-bit two's complement in place: zero below the lowest non-zero
+        // limb f, -x at f, ~x above; limbs beyond L are the sign extension
+        if (neg)
+            for (int l = lane; l < L; l += 32) {
+                const uint32_t v = row[l];
+                row[l] = l < f ? 0u : (l == f ? 0u - v : ~v);
+            }
+        __syncwarp();
+        const uint32_t ext = neg ? 0xffffffffu : 0u;
         unsigned carry_in = 0;
         for (int j0 = 0; j0 < K; j0 += 32) {
             const int j = j0 + lane;
@@ -107,10 +111,10 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
             if (j < K) {
                 const int64_t bit = (int64_t)M * j;
                 const int l0 = (int)(bit >> 5), sh = (int)(bit & 31);
-                const uint64_t lo = (uint64_t)twos_limb(row, L, neg, f, l0) |
-                                    ((uint64_t)twos_limb(row, L, neg, f, l0 + 1) << 32);
-                uint64_t v = lo;
-                if (sh) v = (lo >> sh) | ((uint64_t)twos_limb(row, L, neg, f, l0 + 2) << (64 - sh));
+                const uint64_t lo = (uint64_t)(l0 < L ? row[l0] : ext) |
+                                    ((uint64_t)(l0 + 1 < L ? row[l0 + 1] : ext) << 32);
+                uint64_t v = lo >> sh;
+                if (sh + M > 64) v |= (uint64_t)(l0 + 2 < L ? row[l0 + 2] : ext) << (64 - sh);
                 u = v & mmask;
             }
             const bool inner = j < K - 1;
@@ -138,6 +142,10 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         const PrimeConst &pc = P.pc[t];
         const uint32_t p = pc.p, p2 = pc.p2;
         const uint2 one = make_uint2(1u, pc.one_s), c32 = make_uint2(pc.c32, pc.c32_s);
+        for (int j = threadIdx.x; j < K; j += blockDim.x) tw_twist[j] = __ldg(pc.tx_f + j);
+        for (int q = threadIdx.x; q < Y2; q += blockDim.x)
+            tw_rows[q] = __ldg(pc.ty_f + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
+        __syncthreads();
         // 2. residues (cyclic half) and twisted residues theta^j a_ij (negacyclic half)
         for (int e = threadIdx.x; e < nr * K; e += blockDim.x) {
             const int i2 = e >> logK, j = e & (K - 1);
@@ -148,9 +156,13 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
             if (d < 0 && r) r = p - r;
             uint32_t *trow = tile + (size_t)i2 * pitch;
             trow[j] = r;
-            trow[K + j] = shoup(r, __ldg(pc.tx_f + j), p);
+            trow[K + j] = shoup(r, tw_twist[j], p);
         }
-        for (int e = threadIdx.x; e < (Y2 - nr) * twoK; e += blockDim.x) {
+        // rows nr.. are zero padding; when they cover the upper half the first
+        // y stage does not read that half at all
+        const bool upper_zero = Y2 >= 2 && 2 * nr <= Y2;
+        const int zlim = upper_zero ? Y2 / 2 : Y2;
+        for (int e = threadIdx.x; e < (zlim - nr) * twoK; e += blockDim.x) {
             const int i2 = nr + (e >> (logK + 1)), col = e & (twoK - 1);
             tile[(size_t)i2 * pitch + col] = 0u;
         }
@@ -162,13 +174,12 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         }
         // 4. y step A: length-Y2 DFT down every column
         const TileMap ym{tile, twoK, twoK, 1, 0, pitch};
-        ntt_forward(ym, P.logY2, pc.ty_f, P.logY, p, p2);
+        ntt_forward(ym, P.logY2, pc.ty_f, P.logY, p, p2, upper_zero);
         // 5. step B twiddle, full reduction, store rows (k2, i1)
         uint32_t *Zt = P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK;
         for (int e = threadIdx.x; e < Y2 * twoK; e += blockDim.x) {
             const int pos = e >> (logK + 1), col = e & (twoK - 1);
-            const uint32_t k2 = bitrev((uint32_t)pos, P.logY2);
-            const uint2 w = __ldg(pc.ty_f + (size_t)i1 * k2);
+            const uint2 w = tw_rows[pos];
             const uint32_t v = red(shoup(tile[(size_t)pos * pitch + col], w, p), p);
             Zt[((size_t)pos * Y1 + i1) * twoK + col] = v;
         }
@@ -479,6 +490,8 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
     uint32_t *R = reinterpret_cast<uint32_t *>(smem);  // [r][Y2][pitch]
     const int lc1 = P.lc + 1;
     uint4 *sources = reinterpret_cast<uint4 *>(smem + (((size_t)r * plane * 4 + 15) & ~(size_t)15));  // [lc1]
+    uint2 *tw_rows = reinterpret_cast<uint2 *>(sources + lc1);  // omega_Y^{-i1 k2(pos)}, pos < Y2
+    uint2 *tw_untw = tw_rows + Y2;                               // scale theta^{-j}, j < K
     for (int q = threadIdx.x; q < lc1; q += blockDim.x)
         sources[q] = M >= 32 ? limb_sources(q, M, r, twoK) : make_uint4(contrib_range(q, M, r, twoK), 0, 0, 0);
 
@@ -506,12 +519,14 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
             case 4: cp_async_wait<4>(); break;
             default: cp_async_wait<5>(); break;
         }
+        for (int q = threadIdx.x; q < Y2; q += blockDim.x)
+            tw_rows[q] = __ldg(pc.ty_i + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
+        for (int j = threadIdx.x; j < K; j += blockDim.x) tw_untw[j] = __ldg(pc.untw + j);
         __syncthreads();
         for (int e = threadIdx.x; e < Y2 * twoK; e += blockDim.x) {
             const int pos = e >> (logK + 1), col = e & (twoK - 1);
-            const uint32_t k2 = bitrev((uint32_t)pos, P.logY2);
             uint32_t *x = Rt + (size_t)pos * pitch + col;
-            *x = shoup(*x, __ldg(pc.ty_i + (size_t)i1 * k2), p);
+            *x = shoup(*x, tw_rows[pos], p);
         }
         __syncthreads();
         const TileMap ym{Rt, twoK, twoK, 1, 0, pitch};
@@ -525,7 +540,7 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
             const int i2 = e >> logK, j = e & (K - 1);
             uint32_t *row = Rt + (size_t)i2 * pitch;
             const uint32_t u = shoup(row[j], sc, p);
-            const uint32_t v = shoup(row[K + j], __ldg(pc.untw + j), p);
+            const uint32_t v = shoup(row[K + j], tw_untw[j], p);
             row[j] = red(red(u + v, p2), p);
             row[K + j] = red(red(u - v + p2, p2), p);
         }

@@ -152,10 +152,15 @@ struct Tiles {
     size_t smem_fwd, smem_mid, smem_inv;
 };
 
-size_t fwd_smem(int64_t Y2, int K) { return (size_t)Y2 * K * 8 + (size_t)Y2 * (2 * K + 1) * 4; }
+size_t fwd_smem(int64_t Y2, int K) {
+    // digits, twist and row twiddles, signs, tile
+    return (size_t)Y2 * K * 8 + ((size_t)K + (size_t)Y2) * 8 + (((size_t)Y2 + 15) & ~(size_t)15) +
+           (size_t)Y2 * (2 * K + 1) * 4;
+}
 size_t inv_smem(int64_t Y2, int K, int r, int lc) {
     size_t sources = ((size_t)lc + 1) * 16;  // one uint4 per limb
-    return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources;
+    size_t tables = ((size_t)Y2 + (size_t)K) * 8;  // row twiddles, untwist
+    return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources + tables;
 }
 size_t mid_smem(int64_t Y1, int S, bool tables) {
     return ((size_t)2 * Y1 * (S + 1) + 16) * 4 + (tables ? (size_t)2 * Y1 * 8 : 0);

@@ -80,6 +80,28 @@ __device__ __forceinline__ void dft_dif(uint32_t (&x)[R], const Roots<R> &rt, ui
     }
 }
 
+// dft_dif for inputs whose upper half x[R/2..R) is zero: the first level
+// reduces to x[k + R/2] = x[k] omega_R^k.
+template <int R>
+__device__ __forceinline__ void dft_dif_hz(uint32_t (&x)[R], const Roots<R> &rt, uint32_t p, uint32_t p2) {
+    x[R / 2] = x[0];
+#pragma unroll
+    for (int k = 1; k < R / 2; ++k) x[k + R / 2] = shoup(x[k], rt.w[k], p);
+#pragma unroll
+    for (int h = R / 4; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                if (k == 0)
+                    bf_unit(x[b], x[b + h], p2);
+                else
+                    bf_dif(x[b + k], x[b + k + h], rt.w[k * (R / (2 * h))], p, p2);
+            }
+        }
+    }
+}
+
 // In-register inverse DFT (roots omega_R^{-j}), bit-reversed in, natural out.
 template <int R>
 __device__ __forceinline__ void dft_dit(uint32_t (&x)[R], const Roots<R> &rt, uint32_t p, uint32_t p2) {
@@ -128,7 +150,8 @@ __device__ __forceinline__ uint32_t *group_base(const TileMap &m, int lT, int lt
 
 // One forward stage of radix R at sub-block length Lc = 2^logLc (L = 2^logL).
 // tw: table of omega_T^e (T = 2^logT), T a multiple of L.
-template <int R, bool SM>
+// HZ: the second half of every group's inputs is zero (not read).
+template <int R, bool SM, bool HZ = false>
 __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
                                           uint32_t p2) {
@@ -149,19 +172,28 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
         uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
         uint32_t x[R];
         if (Lp > 1) {
-            // twiddles omega_Lc^{n1 k2} first: their latency hides behind the DFT
+            // twiddles omega_Lc^{n1 k2} first: their latency hides behind the
+            // DFT; entry n1 k2 2^tsh of the table is step * k2 for a per-group step
+            const uint2 *wb = tw;
+            const uint32_t step = (uint32_t)n1 << tsh;
             uint2 w[R];
 #pragma unroll
-            for (int m = 1; m < R; ++m) w[m] = tload<SM>(tw + ((uint32_t)(n1 * brev_c<R>(m)) << tsh));
+            for (int m = 1; m < R; ++m) w[m] = tload<SM>(wb + step * (uint32_t)brev_c<R>(m));
 #pragma unroll
-            for (int m = 0; m < R; ++m) x[m] = base[m * st];
-            dft_dif<R>(x, rt, p, p2);
+            for (int m = 0; m < (HZ ? R / 2 : R); ++m) x[m] = base[m * st];
+            if (HZ)
+                dft_dif_hz<R>(x, rt, p, p2);
+            else
+                dft_dif<R>(x, rt, p, p2);
 #pragma unroll
             for (int m = 1; m < R; ++m) x[m] = shoup(x[m], w[m], p);
         } else {  // last stage: every twiddle is 1
 #pragma unroll
-            for (int m = 0; m < R; ++m) x[m] = base[m * st];
-            dft_dif<R>(x, rt, p, p2);
+            for (int m = 0; m < (HZ ? R / 2 : R); ++m) x[m] = base[m * st];
+            if (HZ)
+                dft_dif_hz<R>(x, rt, p, p2);
+            else
+                dft_dif<R>(x, rt, p, p2);
         }
 #pragma unroll
         for (int m = 0; m < R; ++m) base[m * st] = x[m];
@@ -190,9 +222,10 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
         uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
         uint32_t x[R];
         if (Lp > 1) {
+            const uint32_t step = (uint32_t)n1 << tsh;
             uint2 w[R];
 #pragma unroll
-            for (int m = 1; m < R; ++m) w[m] = tload<SM>(tw + ((uint32_t)(n1 * brev_c<R>(m)) << tsh));
+            for (int m = 1; m < R; ++m) w[m] = tload<SM>(tw + step * (uint32_t)brev_c<R>(m));
 #pragma unroll
             for (int m = 0; m < R; ++m) x[m] = base[m * st];
 #pragma unroll
@@ -219,7 +252,15 @@ __device__ __forceinline__ void stage_split(int logL, int &nst, int &base, int &
 template <bool FWD, bool SM>
 __device__ __forceinline__ void run_stage(int b, const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
-                                          uint32_t p2) {
+                                          uint32_t p2, bool hz = false) {
+    if (FWD && hz) {
+        switch (b) {
+            case 1: stage_dif<2, SM, true>(M, logL, logLc, tw, logT, p, p2); return;
+            case 2: stage_dif<4, SM, true>(M, logL, logLc, tw, logT, p, p2); return;
+            case 3: stage_dif<8, SM, true>(M, logL, logLc, tw, logT, p, p2); return;
+            default: stage_dif<16, SM, true>(M, logL, logLc, tw, logT, p, p2); return;
+        }
+    }
     switch (b) {
         case 1: FWD ? stage_dif<2, SM>(M, logL, logLc, tw, logT, p, p2) : stage_dit<2, SM>(M, logL, logLc, tw, logT, p, p2); break;
         case 2: FWD ? stage_dif<4, SM>(M, logL, logLc, tw, logT, p, p2) : stage_dit<4, SM>(M, logL, logLc, tw, logT, p, p2); break;
@@ -230,15 +271,17 @@ __device__ __forceinline__ void run_stage(int b, const TileMap &M, int logL, int
 
 // Full forward transform of length 2^logL on every transform of the map
 // (natural order in, bit-reversed order out).  Values in [0, 2p).
+// upper_zero: the second half of every transform's input is zero and is
+// not read (the zero padding of an acyclic convolution).
 template <bool SM = false>
 __device__ __forceinline__ void ntt_forward(const TileMap &M, int logL, const uint2 *__restrict__ tw,
-                                            int logT, uint32_t p, uint32_t p2) {
+                                            int logT, uint32_t p, uint32_t p2, bool upper_zero = false) {
     int nst, base, extra;
     stage_split(logL, nst, base, extra);
     int logLc = logL;
     for (int i = 0; i < nst; ++i) {
         const int b = base + (i < extra ? 1 : 0);
-        run_stage<true, SM>(b, M, logL, logLc, tw, logT, p, p2);
+        run_stage<true, SM>(b, M, logL, logLc, tw, logT, p, p2, upper_zero && i == 0);
         logLc -= b;
     }
 }
