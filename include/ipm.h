@@ -82,9 +82,10 @@ typedef struct {
  *   r : number of 30-bit Fourier primes (1..6); needs prod p > 4H (§2.1)
  *   y2: rows per forward/inverse tile (power of two dividing Y)
  *   s : columns per middle-pass tile (power of two dividing 2K)
+ *   y1b: split the middle transform in two (power of two > 1 dividing Y/y2)
  */
 typedef struct {
-    int32_t K, M, r, y2, s;
+    int32_t K, M, r, y2, s, y1b;
 } ipm_params;
 
 /* What a plan chose (ipm_choose / ipm_get_info). */
@@ -94,6 +95,7 @@ typedef struct {
     int32_t K, M, N, r;       /* split N = K*M and number of primes */
     int64_t Y, Y1, Y2;        /* y-transform length Y = Y1*Y2 >= nc */
     int32_t S;                /* middle-pass column slice */
+    int64_t Y1b;              /* outer split of Y1 (1 = none) */
     uint32_t primes[8];       /* p_0 > p_1 > ... (r used) */
     double log2_modulus;      /* log2(prod p) */
     double log2_bound;        /* log2(4H), H = min(na,nb)*K*2^(2M-2) */

@@ -35,7 +35,7 @@ class Shape(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("M", ctypes.c_int32), ("r", ctypes.c_int32),
-                ("y2", ctypes.c_int32), ("s", ctypes.c_int32)]
+                ("y2", ctypes.c_int32), ("s", ctypes.c_int32), ("y1b", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -43,7 +43,8 @@ class PlanInfo(ctypes.Structure):
                 ("la", ctypes.c_int32), ("lb", ctypes.c_int32), ("lc", ctypes.c_int32),
                 ("K", ctypes.c_int32), ("M", ctypes.c_int32), ("N", ctypes.c_int32),
                 ("r", ctypes.c_int32), ("Y", ctypes.c_int64), ("Y1", ctypes.c_int64),
-                ("Y2", ctypes.c_int64), ("S", ctypes.c_int32), ("primes", ctypes.c_uint32 * 8),
+                ("Y2", ctypes.c_int64), ("S", ctypes.c_int32), ("Y1b", ctypes.c_int64),
+                ("primes", ctypes.c_uint32 * 8),
                 ("log2_modulus", ctypes.c_double), ("log2_bound", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -99,10 +100,10 @@ def _check(st: int, what: str):
         raise IpmError(st, what)
 
 
-def _params(K=0, M=0, r=0, y2=0, s=0):
-    if not (K or M or r or y2 or s):
+def _params(K=0, M=0, r=0, y2=0, s=0, y1b=0):
+    if not (K or M or r or y2 or s or y1b):
         return None
-    return Params(K, M, r, y2, s)
+    return Params(K, M, r, y2, s, y1b)
 
 
 def choose(na: int, nb: int, bits_a: int, bits_b: int, **overrides) -> dict:

@@ -59,6 +59,12 @@ struct KParams {
     int64_t Y, Y1, Y2;
     int32_t logY, logY1, logY2, S, logS;
     int32_t mid_tables_in_smem;  // middle pass keeps its omega_Y1 tables in shared memory
+    // Three-level split of the middle transform (Y1 = Y1a * Y1b, Y1b > 1):
+    // an outer pass does the length-Y1b transforms over i1b (rows i1a +
+    // Y1a i1b) and the twiddle omega_Y1^{i1a k1b}; the middle pass then
+    // works on length-Y1a columns.  Y1b = 1: no split.
+    int64_t Y1a, Y1b;
+    int32_t logY1a, logY1b, S2, logS2;
     PrimeConst pc[RMAX];
     // Garner: ginv[t][s] = p_s^{-1} mod p_t (s < t), with Shoup quotients.
     uint32_t ginv[RMAX][RMAX];
@@ -74,7 +80,7 @@ struct KParams {
 struct ShapePlan {
     ipm_plan_info info;
     KParams kp;           // pointers filled in by ipm_plan
-    size_t smem_fwd, smem_mid, smem_inv;
+    size_t smem_fwd, smem_mid, smem_inv, smem_outer;
     size_t z_words;       // workspace words
     size_t table_words;   // table uint2 entries per prime
 };
@@ -97,6 +103,11 @@ int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint
                    const uint32_t *b, const uint8_t *bn, void *stream);
 int launch_middle(const KParams &kp, size_t smem, void *stream);
 int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, void *stream);
+int launch_outer(const KParams &kp, size_t smem, bool forward, void *stream);
+// The whole launch sequence of one product (forward, [outer], middle,
+// [outer inverse], inverse).  Returns 0 or -1 on a launch error.
+int launch_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                   const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
 int set_kernel_attributes();
 
 // One group of a batched call: products that share the kernel variants,

@@ -194,27 +194,28 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
 __device__ __forceinline__ const uint2 *pc_tables_f(const KParams &P, int t) { return P.pc[t].t1_f; }
 __device__ __forceinline__ const uint2 *pc_tables_i(const KParams &P, int t) { return P.pc[t].t1_i; }
 
-// Pass 2 on one tile: columns [cs S, cs S + S) of the rows (pos, i1), i1 < Y1,
-// prime t.  SMTW: the omega_Y1 tables are copied to shared memory (else read
-// from global memory through the non-coherent cache).
+// Pass 2 on one tile: columns [cs S, cs S + S) of the rows (pos, i1), prime t,
+// for i1 = Y1a pb + i1a, i1a < Y1a (without a split Y1a = Y1 and pb = 0).
+// SMTW: the omega_Y1 tables are copied to shared memory (else read from
+// global memory through the non-coherent cache).
 template <bool SMTW>
-__device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int t) {
+__device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int pb, int t) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = P.S, logS = P.logS;
     const int pitch = S + 1;  // odd pitch for conflict-free strided gathers
     const int twoK = 2 * P.K;
-    const int Y1 = (int)P.Y1;
-    uint2 *twf_s = reinterpret_cast<uint2 *>(smem);     // omega_Y1^e, e < Y1
+    const int Y1 = (int)P.Y1a;  // this tile's column length
+    uint2 *twf_s = reinterpret_cast<uint2 *>(smem);     // omega_Y1^e, e < Y1 (no split)
     uint2 *twi_s = twf_s + Y1;                          // omega_Y1^{-e}
     const uint2 *twf = SMTW ? twf_s : pc_tables_f(P, t);
     const uint2 *twi = SMTW ? twi_s : pc_tables_i(P, t);
-    uint32_t *A = reinterpret_cast<uint32_t *>(SMTW ? (void *)(twi_s + Y1) : (void *)smem);  // [Y1][pitch]
+    uint32_t *A = reinterpret_cast<uint32_t *>(SMTW ? (void *)(twi_s + Y1) : (void *)smem);  // [Y1a][pitch]
     uint32_t *B = A + (size_t)Y1 * pitch + 16;          // [Y1][pitch], shifted 16 banks
     const PrimeConst &pc = P.pc[t];
     const uint32_t p = pc.p, p2 = pc.p2;
     uint32_t *ZA = P.Z + (size_t)(t * 2 + 0) * (size_t)P.Y * twoK;
     const uint32_t *ZB = P.Z + (size_t)(t * 2 + 1) * (size_t)P.Y * twoK;
-    const size_t base = (size_t)pos * Y1 * twoK + (size_t)cs * S;
+    const size_t base = ((size_t)pos * P.Y1 + (size_t)P.Y1a * pb) * twoK + (size_t)cs * S;
     // A's slice, then B's, as two asynchronous copy groups: B is still in
     // flight while A is transformed
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
@@ -237,11 +238,11 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     __syncthreads();
     // y step C (omega_Y1 = omega_Y^Y2) on the S columns of A, then of B
     const TileMap am{A, S, S, 1, 0, pitch};
-    ntt_forward<SMTW>(am, P.logY1, twf, P.logY1, p, p2);
+    ntt_forward<SMTW>(am, P.logY1a, twf, P.logY1, p, p2);
     cp_async_wait<0>();
     __syncthreads();
     const TileMap bm{B, S, S, 1, 0, pitch};
-    ntt_forward<SMTW>(bm, P.logY1, twf, P.logY1, p, p2);
+    ntt_forward<SMTW>(bm, P.logY1a, twf, P.logY1, p, p2);
     // pointwise product in Montgomery form: A*B*2^-32 (the 2^32 is put back
     // by the scale factor of the inverse pass)
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
@@ -249,10 +250,57 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
         A[i] = montmul(A[i], B[i], p, pc.mont);
     }
     __syncthreads();
-    ntt_inverse<SMTW>(am, P.logY1, twi, P.logY1, p, p2);
+    ntt_inverse<SMTW>(am, P.logY1a, twi, P.logY1, p, p2);
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
         const int i1 = e >> logS, c = e & (S - 1);
         ZA[base + (size_t)i1 * twoK + c] = red(A[i1 * pitch + c], p);
+    }
+}
+
+// Outer pass of a split middle transform, on one tile: columns
+// [cs S2, cs S2 + S2) of the rows (pos, i1a + Y1a i1b), i1b < Y1b, prime t,
+// operand op.  Forward: length-Y1b DFT over i1b, then the twiddle
+// omega_Y1^{i1a k1b}.  Inverse: the twiddle's inverse, then the inverse DFT.
+template <bool FWD>
+__device__ __forceinline__ void outer_tile(const KParams &P, int cs, int pos, int i1a, int t, int op) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int S2 = P.S2, logS2 = P.logS2;
+    const int pitch = S2 + 1;
+    const int twoK = 2 * P.K;
+    const int Y1b = (int)P.Y1b;
+    uint32_t *T = reinterpret_cast<uint32_t *>(smem);                      // [Y1b][pitch]
+    uint2 *tw_rows = reinterpret_cast<uint2 *>(T + ((Y1b * pitch + 1) & ~1));  // Y1b entries
+    const PrimeConst &pc = P.pc[t];
+    const uint32_t p = pc.p, p2 = pc.p2;
+    uint32_t *Zt = P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK;
+    const size_t row0 = (size_t)pos * P.Y1 + i1a;
+    const size_t rstride = (size_t)P.Y1a * twoK;
+    for (int e = threadIdx.x; e < Y1b * S2; e += blockDim.x) {
+        const int ib = e >> logS2, c = e & (S2 - 1);
+        cp_async4(T + ib * pitch + c, Zt + row0 * twoK + ib * rstride + (size_t)cs * S2 + c);
+    }
+    cp_async_commit();
+    const uint2 *tab = FWD ? pc.t1_f : pc.t1_i;
+    for (int q = threadIdx.x; q < Y1b; q += blockDim.x)
+        tw_rows[q] = __ldg(tab + (size_t)i1a * bitrev((uint32_t)q, P.logY1b));
+    cp_async_wait<0>();
+    __syncthreads();
+    const TileMap m{T, S2, S2, 1, 0, pitch};
+    if (FWD) {
+        ntt_forward(m, P.logY1b, pc.t1_f, P.logY1, p, p2);
+    } else {
+        for (int e = threadIdx.x; e < Y1b * S2; e += blockDim.x) {
+            const int i = (e >> logS2) * pitch + (e & (S2 - 1));
+            T[i] = shoup(T[i], tw_rows[e >> logS2], p);
+        }
+        __syncthreads();
+        ntt_inverse(m, P.logY1b, pc.t1_i, P.logY1, p, p2);
+    }
+    for (int e = threadIdx.x; e < Y1b * S2; e += blockDim.x) {
+        const int ib = e >> logS2, c = e & (S2 - 1);
+        uint32_t v = T[ib * pitch + c];
+        v = FWD ? red(shoup(v, tw_rows[ib], p), p) : red(v, p);
+        Zt[row0 * twoK + ib * rstride + (size_t)cs * S2 + c] = v;
     }
 }
 
@@ -596,7 +644,20 @@ k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a, con
 
 template <bool SMTW>
 __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant__ KParams P) {
-    mid_tile<SMTW>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+    // blockIdx.y = pos * Y1b + pb
+    mid_tile<SMTW>(P, blockIdx.x, blockIdx.y >> P.logY1b, blockIdx.y & (P.Y1b - 1), blockIdx.z);
+}
+
+// grid: x = (pos * Y1a + i1a) * (2K/S2) + cs; y = 2t + op forward (both
+// operands), y = t inverse (the product, held in operand A's slab)
+template <bool FWD>
+__global__ void __launch_bounds__(THREADS_MID, 1) k_outer(const __grid_constant__ KParams P) {
+    const int lncs = P.logK + 1 - P.logS2;
+    const int cs = blockIdx.x & ((1 << lncs) - 1);
+    const uint32_t rest = blockIdx.x >> lncs;
+    const int t = FWD ? (int)(blockIdx.y >> 1) : (int)blockIdx.y;
+    const int op = FWD ? (int)(blockIdx.y & 1) : 0;
+    outer_tile<FWD>(P, cs, (int)(rest >> P.logY1a), (int)(rest & (P.Y1a - 1)), t, op);
 }
 
 template <int NT>
@@ -622,8 +683,8 @@ kb_middle(const KParams *__restrict__ Ps, const uint2 *__restrict__ items) {
     const KParams &P = Ps[it.x];
     const int ncs = 2 * P.K / P.S;
     const int cs = (int)(it.y % (uint32_t)ncs);
-    const int rest = (int)(it.y / (uint32_t)ncs);
-    mid_tile<SMTW>(P, cs, rest % (int)P.Y2, rest / (int)P.Y2);
+    const int rest = (int)(it.y / (uint32_t)ncs);  // (t, pos) of an unsplit plan
+    mid_tile<SMTW>(P, cs, rest % (int)P.Y2, 0, rest / (int)P.Y2);
 }
 
 template <int NT>
@@ -650,6 +711,8 @@ int set_kernel_attributes() {
     set((const void *)k_middle<false>, SMEM_MID_MAX);
     set((const void *)k_inverse<THREADS_INV>, SMEM_INV_MAX);
     set((const void *)k_inverse<1024>, SMEM_INV_MAX);
+    set((const void *)k_outer<true>, SMEM_MID_MAX);
+    set((const void *)k_outer<false>, SMEM_MID_MAX);
     set((const void *)kb_forward<THREADS_FWD>, SMEM_FWD_MAX);
     set((const void *)kb_forward<1024>, SMEM_FWD_MAX);
     set((const void *)kb_middle<true>, SMEM_MID_MAX);
@@ -699,8 +762,18 @@ int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+int launch_outer(const KParams &kp, size_t smem, bool forward, void *stream) {
+    dim3 grid((unsigned)((2 * kp.K / kp.S2) * kp.Y2 * kp.Y1a), (unsigned)(forward ? 2 * kp.r : kp.r), 1);
+    if (forward)
+        k_outer<true><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
+    else
+        k_outer<false><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
+    g_launches.fetch_add(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_middle(const KParams &kp, size_t smem, void *stream) {
-    dim3 grid((unsigned)(2 * kp.K / kp.S), (unsigned)kp.Y2, (unsigned)kp.r);
+    dim3 grid((unsigned)(2 * kp.K / kp.S), (unsigned)(kp.Y2 * kp.Y1b), (unsigned)kp.r);
     if (kp.mid_tables_in_smem)
         k_middle<true><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
     else
@@ -717,6 +790,16 @@ int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, voi
         k_inverse<1024><<<grid, 1024, smem, (cudaStream_t)stream>>>(kp, c, cn);
     g_launches.fetch_add(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                   const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream) {
+    const KParams &kp = sp.kp;
+    if (launch_forward(kp, sp.smem_fwd, a, an, b, bn, stream)) return -1;
+    if (kp.Y1b > 1 && launch_outer(kp, sp.smem_outer, true, stream)) return -1;
+    if (launch_middle(kp, sp.smem_mid, stream)) return -1;
+    if (kp.Y1b > 1 && launch_outer(kp, sp.smem_outer, false, stream)) return -1;
+    return launch_inverse(kp, sp.smem_inv, c, cn, stream);
 }
 
 }  // namespace ipm

@@ -106,9 +106,7 @@ extern "C" ipm_status ipm_mul_noalloc(const ipm_shape *shape, const uint32_t *a,
     }
     sp.kp.Z = Z;
     sp.kp.err = err;
-    if (ipm::launch_forward(sp.kp, sp.smem_fwd, a, a_neg, b, b_neg, stream)) return IPM_ERR_CUDA;
-    if (ipm::launch_middle(sp.kp, sp.smem_mid, stream)) return IPM_ERR_CUDA;
-    if (ipm::launch_inverse(sp.kp, sp.smem_inv, c, c_neg, stream)) return IPM_ERR_CUDA;
+    if (ipm::launch_product(sp, a, a_neg, b, b_neg, c, c_neg, stream)) return IPM_ERR_CUDA;
     int h = 0;
     if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return IPM_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return IPM_ERR_CUDA;

@@ -149,7 +149,9 @@ struct Tiles {
     int64_t Y2;
     int32_t S;
     bool mid_tables;
-    size_t smem_fwd, smem_mid, smem_inv;
+    int64_t Y1b;   // outer split of the middle transform (1 = none)
+    int32_t S2;    // outer pass column slice
+    size_t smem_fwd, smem_mid, smem_inv, smem_outer;
 };
 
 size_t fwd_smem(int64_t Y2, int K) {
@@ -165,52 +167,76 @@ size_t inv_smem(int64_t Y2, int K, int r, int lc) {
 size_t mid_smem(int64_t Y1, int S, bool tables) {
     return ((size_t)2 * Y1 * (S + 1) + 16) * 4 + (tables ? (size_t)2 * Y1 * 8 : 0);
 }
+// outer pass: one operand's Y1b x S2 tile plus its Y1b row twiddles
+size_t outer_smem(int64_t Y1b, int S2) { return (size_t)Y1b * (S2 + 1) * 4 + (size_t)Y1b * 8; }
 
 // Tile shapes: Y2 rows per forward/inverse tile, S columns per middle tile
 // (Y1 = Y / Y2 is the middle pass's column length).  Hard limit: every pass
 // fits one block's shared memory.  Preferences, in order: middle slices of
 // at least 8 columns (32-byte DRAM sectors), an inverse tile small enough
-// for two CTAs per SM, a forward tile small enough for three, and Y2 close
-// to max(32, Y / 2048) (the middle pass's twiddle tables stay small).
-bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force, Tiles &t) {
+// for two CTAs per SM, a forward tile small enough for three, no split of
+// the middle transform (a split costs an extra pass over the data), and Y2
+// close to max(32, Y / 2048).  When Y1 is long, the middle transform may be
+// split as Y1 = Y1a * Y1b (Y1a <= 2048) with an outer pass over Y1b.
+bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force, int64_t y1b_force,
+                  Tiles &t) {
     const int64_t target = std::max<int64_t>(std::min<int64_t>(32, Y), Y / 2048);
     bool found = false;
     double best = 0;
+    auto widest = [&](int64_t rows, bool tab, int force) {
+        for (int s = std::min(2 * K, 32); s >= 1; s >>= 1) {
+            if (force && s != force) continue;
+            if (mid_smem(rows, s, tab) <= SMEM_MID_MAX) return s;
+        }
+        return 0;
+    };
     for (int64_t Y2 = 1; Y2 <= Y && Y2 <= 8192; Y2 <<= 1) {
         if (y2_force && Y2 != y2_force) continue;
         const size_t fw = fwd_smem(Y2, K), iv = inv_smem(Y2, K, r, lc);
         if (fw > SMEM_FWD_MAX || iv > SMEM_INV_MAX) continue;
         const int64_t Y1 = Y / Y2;
-        // widest slice that fits, with the twiddle tables in shared memory
-        // if possible, else read from global memory
-        int S = 0;
-        bool tab = true;
-        for (int pass = 0; pass < 2 && S == 0; ++pass) {
-            tab = pass == 0;
-            for (int s = std::min(2 * K, 32); s >= 1; s >>= 1) {
-                if (s_force && s != s_force) continue;
-                if (mid_smem(Y1, s, tab) <= SMEM_MID_MAX) { S = s; break; }
+        for (int64_t Y1b = 1; Y1b <= Y1; Y1b <<= 1) {
+            if (y1b_force ? Y1b != y1b_force : (Y1b > 1 && Y1 / Y1b < 512)) continue;
+            const int64_t Y1a = Y1 / Y1b;
+            if (Y1b > 1 && Y1a > 2048) continue;
+            if (Y1b > 1 && Y1a < 2) continue;
+            // middle slice, with the twiddle tables in shared memory if possible
+            // (never for a split: the tables span all of Y1)
+            bool tab = Y1b == 1;
+            int S = tab ? widest(Y1a, true, s_force) : 0;
+            if (S > 0 && S < 8 && S < 2 * K && !s_force) {
+                const int s2 = widest(Y1a, false, 0);  // wider without the tables
+                if (s2 > S) { S = s2; tab = false; }
             }
-            if (tab && S > 0 && S < 8 && S < 2 * K && !s_force) {
-                // a wider slice without the tables beats a narrow one with them
-                for (int s = std::min(2 * K, 32); s > S; s >>= 1)
-                    if (mid_smem(Y1, s, false) <= SMEM_MID_MAX) { S = s; tab = false; break; }
+            if (S == 0) {
+                tab = false;
+                S = widest(Y1a, false, s_force);
             }
-        }
-        if (s_force && (s_force > 2 * K || (s_force & (s_force - 1)))) S = 0;
-        if (S == 0) continue;
-        double score = (S >= 8 || S == 2 * K ? 0 : 8) + (iv <= SMEM_INV_2PERSM ? 0 : 4) +
-                       (fw <= SMEM_FWD_3PERSM ? 0 : 2) + (tab ? 0 : 1) +
-                       0.1 * std::abs(ilog2((uint64_t)Y2) - ilog2((uint64_t)target));
-        if (!found || score < best) {
-            found = true;
-            best = score;
-            t.Y2 = Y2;
-            t.S = S;
-            t.mid_tables = tab;
-            t.smem_fwd = fw;
-            t.smem_mid = mid_smem(Y1, S, tab);
-            t.smem_inv = iv;
+            if (s_force && (s_force > 2 * K || (s_force & (s_force - 1)))) S = 0;
+            if (S == 0) continue;
+            int S2 = 0;
+            if (Y1b > 1) {
+                for (int s = std::min(2 * K, 32); s >= 1; s >>= 1)
+                    if (outer_smem(Y1b, s) <= SMEM_MID_MAX) { S2 = s; break; }
+                if (S2 == 0) continue;
+            }
+            const double score = (S >= 8 || S == 2 * K ? 0 : 8) + (iv <= SMEM_INV_2PERSM ? 0 : 4) +
+                                 (fw <= SMEM_FWD_3PERSM ? 0 : 2) + (tab ? 0 : 1) + (Y1b > 1 ? 3 : 0) +
+                                 (Y1b > 1 && S2 < 8 && S2 < 2 * K ? 8 : 0) +
+                                 0.1 * std::abs(ilog2((uint64_t)Y2) - ilog2((uint64_t)target));
+            if (!found || score < best) {
+                found = true;
+                best = score;
+                t.Y2 = Y2;
+                t.S = S;
+                t.mid_tables = tab;
+                t.Y1b = Y1b;
+                t.S2 = S2 ? S2 : 1;
+                t.smem_fwd = fw;
+                t.smem_mid = mid_smem(Y1a, S, tab);
+                t.smem_inv = iv;
+                t.smem_outer = Y1b > 1 ? outer_smem(Y1b, S2) : 0;
+            }
         }
     }
     return found;
@@ -239,7 +265,8 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
     if (sh.deg_a >= (1ll << 40) || sh.deg_b >= (1ll << 40)) return IPM_ERR_UNSUPPORTED;
     ipm_params P{};
     if (prm) P = *prm;
-    if (P.K < 0 || P.M < 0 || P.r < 0 || P.y2 < 0 || P.s < 0) return IPM_ERR_ARG;
+    if (P.K < 0 || P.M < 0 || P.r < 0 || P.y2 < 0 || P.s < 0 || P.y1b < 0) return IPM_ERR_ARG;
+    if (P.y1b == 1 || (P.y1b & (P.y1b - 1))) return IPM_ERR_ARG;
     if (P.K && (P.K < 2 || (P.K & (P.K - 1)) || P.K > (1 << KMAX_LOG2))) return IPM_ERR_ARG;
     if (P.M && (P.M < 2 || P.M > MMAX)) return IPM_ERR_ARG;
     if (P.r && P.r > RMAX) return IPM_ERR_ARG;
@@ -282,7 +309,7 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
         }
         if (!r || big_cmp(m, bound) <= 0) continue;
         Tiles tl;
-        if (!choose_tiles(Y, K, r, lc, P.y2, P.s, tl)) continue;
+        if (!choose_tiles(Y, K, r, lc, P.y2, P.s, P.y1b, tl)) continue;
         const double pts = (double)r * (double)Y * 2.0 * K;
         const double cost = pts * (3.0 * (logY + logK + 1) + 2.0 * r + 4.0);
         if (found && cost >= best_cost) continue;
@@ -301,6 +328,8 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
         s.smem_fwd = tl.smem_fwd;
         s.smem_mid = tl.smem_mid;
         s.smem_inv = tl.smem_inv;
+        s.smem_outer = tl.smem_outer;
+        I.Y1b = tl.Y1b;
         s.z_words = (size_t)r * 2 * (size_t)Y * 2 * K;
         s.table_words = table_layout(Y, Y / tl.Y2, K).total;
         I.workspace_bytes = s.z_words * 4 + (size_t)r * s.table_words * 8;
@@ -314,9 +343,15 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
         kp.logY = logY; kp.logY2 = ilog2((uint64_t)tl.Y2); kp.logY1 = logY - kp.logY2;
         kp.S = tl.S; kp.logS = ilog2((uint64_t)tl.S);
         kp.mid_tables_in_smem = tl.mid_tables ? 1 : 0;
+        kp.Y1b = tl.Y1b;
+        kp.Y1a = kp.Y1 / tl.Y1b;
+        kp.logY1b = ilog2((uint64_t)tl.Y1b);
+        kp.logY1a = kp.logY1 - kp.logY1b;
+        kp.S2 = tl.S2;
+        kp.logS2 = ilog2((uint64_t)tl.S2);
         best = s;
     }
-    if (!found) return (P.K || P.M || P.r || P.y2 || P.s) ? IPM_ERR_ARG : IPM_ERR_UNSUPPORTED;
+    if (!found) return (P.K || P.M || P.r || P.y2 || P.s || P.y1b) ? IPM_ERR_ARG : IPM_ERR_UNSUPPORTED;
     sp = best;
     return IPM_OK;
 }

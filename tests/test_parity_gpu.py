@@ -100,7 +100,8 @@ def test_small_dense_workload_full():
 
 @pytest.mark.parametrize("kw", [dict(), dict(K=16), dict(K=32), dict(K=8, M=40),
                                 dict(r=4), dict(r=5), dict(r=6), dict(y2=1), dict(y2=64), dict(s=1),
-                                dict(K=64, y2=4, s=2), dict(K=8, M=62), dict(K=256)])
+                                dict(K=64, y2=4, s=2), dict(K=8, M=62), dict(K=256),
+                                dict(y1b=2), dict(y1b=4, s=4), dict(y2=4, y1b=8), dict(K=32, y1b=16)])
 def test_plan_invariance(kw):
     """Every valid (K, M, r, tiles) gives byte-identical output."""
     rng = np.random.default_rng(11)
@@ -268,3 +269,33 @@ def test_huge_mixed_full_size():
     """Half the positions < 2^64, the rest < 2^2048, random positions."""
     sh, a, b = W.huge_mixed(seed=2)
     _sampled_and_identities(sh, a, b)
+
+
+def test_batched_with_split_middle_transform():
+    """Shapes whose middle transform is split run one by one after the
+    grouped launches; the results are the same exact products."""
+    shapes = W.batch_shapes(seed=5, count=5, dmin=300, dmax=900, bmin=64, bmax=300)
+    ops = W.batch_operands(shapes, seed=5)
+    plan = ipm.Plan([(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes], flags=ipm.IPM_SYNC, y1b=2)
+    assert all(info["Y1b"] == 2 for info in plan.infos)
+    dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
+    outs = plan.mul_batched(dev)
+    torch.cuda.synchronize()
+    for (a, b), (c, cn), info in zip(ops, outs, plan.infos):
+        assert_same(ipm.to_host(c, cn), oracle.polymul(a, b, info["lc"]))
+
+
+def test_naturally_split_wide_product():
+    """2^16 coefficients of 16384 bits: the planner splits the middle
+    transform (Y2 = 4, Y1 = 32768 = 2048 x 16)."""
+    rng = np.random.default_rng(17)
+    n, bits = 65536, 16384
+    a = W.random_poly(rng, n, bits)
+    b = W.random_poly(rng, n, bits)
+    got, info = gpu_mul(a, b, bits, bits)
+    assert info["Y1b"] > 1
+    sh = W.Product(n, n, bits, bits)
+    ks = [0, 1, 2, sh.nc - 3, sh.nc - 2, sh.nc - 1]
+    want = oracle.coeffs(ks, a, b, sh.lc)
+    assert_same((got[0][ks], got[1][ks]), want)
+    _whole_output_identities(a, b, got)
