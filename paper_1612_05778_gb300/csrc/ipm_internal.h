@@ -23,7 +23,7 @@ constexpr size_t SMEM_FWD_3PERSM = 74 * 1024;
 constexpr size_t SMEM_INV_2PERSM = 112 * 1024;
 
 constexpr int THREADS_FWD = 256;
-constexpr int THREADS_MID = 1024;
+constexpr int THREADS_MID = 512;
 constexpr int THREADS_INV = 512;
 
 // Device error word bits.

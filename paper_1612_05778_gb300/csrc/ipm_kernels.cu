@@ -236,21 +236,16 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     }
     cp_async_wait<1>();
     __syncthreads();
-    // y step C (omega_Y1 = omega_Y^Y2) on the S columns of A, then of B
+    // y step C (omega_Y1 = omega_Y^Y2) on the S columns of A and of B (B's
+    // copies finish while A is transformed), the pointwise product in
+    // Montgomery form A*B*2^-32 (the 2^32 is put back by the scale factor of
+    // the inverse pass) and the inverse step C, written over A
     const TileMap am{A, S, S, 1, 0, pitch};
-    ntt_forward<SMTW>(am, P.logY1a, twf, P.logY1, p, p2);
-    cp_async_wait<0>();
-    __syncthreads();
     const TileMap bm{B, S, S, 1, 0, pitch};
-    ntt_forward<SMTW>(bm, P.logY1a, twf, P.logY1, p, p2);
-    // pointwise product in Montgomery form: A*B*2^-32 (the 2^32 is put back
-    // by the scale factor of the inverse pass)
-    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
-        const int i = (e >> logS) * pitch + (e & (S - 1));
-        A[i] = montmul(A[i], B[i], p, pc.mont);
-    }
-    __syncthreads();
-    ntt_inverse<SMTW>(am, P.logY1a, twi, P.logY1, p, p2);
+    ntt_convolve<SMTW>(am, bm, P.logY1a, twf, twi, P.logY1, p, p2, pc.mont, [] {
+        cp_async_wait<0>();
+        __syncthreads();
+    });
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
         const int i1 = e >> logS, c = e & (S - 1);
         ZA[base + (size_t)i1 * twoK + c] = red(A[i1 * pitch + c], p);

@@ -286,6 +286,91 @@ __device__ __forceinline__ void ntt_forward(const TileMap &M, int logL, const ui
     }
 }
 
+// The middle of a convolution in one register pass: the last forward stage
+// (radix R, L' = 1) of A and of B, the pointwise product A*B*2^-32
+// (Montgomery), and the first inverse stage, for each group of R
+// consecutive elements; the product is written over A.
+template <int R, bool SM>
+__device__ __forceinline__ void stage_fused_pointwise(const TileMap &MA, const TileMap &MB, int logL,
+                                                      const uint2 *__restrict__ twf,
+                                                      const uint2 *__restrict__ twi, int logT,
+                                                      uint32_t p, uint32_t p2, uint32_t mont) {
+    constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+    Roots<R> rf, ri;
+    load_roots<R, SM>(rf, twf, logT);
+    load_roots<R, SM>(ri, twi, logT);
+    const int total = MA.T << (logL - LR);
+    const int lT = ilog2_if_pow2(MA.T), ltm = ilog2_if_pow2(MA.tm);
+    for (int g = threadIdx.x; g < total; g += blockDim.x) {
+        int blk;
+        uint32_t *ba = group_base(MA, lT, ltm, g, blk) + (blk << LR) * MA.es;
+        uint32_t *bb = group_base(MB, lT, ltm, g, blk) + (blk << LR) * MB.es;
+        uint32_t xa[R], xb[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            xa[m] = ba[m * MA.es];
+            xb[m] = bb[m * MB.es];
+        }
+        dft_dif<R>(xa, rf, p, p2);
+        dft_dif<R>(xb, rf, p, p2);
+#pragma unroll
+        for (int m = 0; m < R; ++m) xa[m] = montmul(xa[m], xb[m], p, mont);
+        dft_dit<R>(xa, ri, p, p2);
+#pragma unroll
+        for (int m = 0; m < R; ++m) ba[m * MA.es] = xa[m];
+    }
+    __syncthreads();
+}
+
+// Convolution core on two sets of transforms: forward A and B (all but the
+// last stage each; A may be run before B's data are ready -- wait_b is
+// called in between), the fused last/pointwise/first-inverse stage, then
+// the remaining inverse stages on A.
+template <bool SM, typename WaitB>
+__device__ __forceinline__ void ntt_convolve(const TileMap &MA, const TileMap &MB, int logL,
+                                             const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
+                                             int logT, uint32_t p, uint32_t p2, uint32_t mont, WaitB wait_b) {
+    int nst, base, extra;
+    stage_split(logL, nst, base, extra);
+    if (nst == 0) {  // length 1: the product of the single values
+        wait_b();
+        for (int t = threadIdx.x; t < MA.T; t += blockDim.x) {
+            int rest;
+            uint32_t *a = group_base(MA, ilog2_if_pow2(MA.T), ilog2_if_pow2(MA.tm), t, rest);
+            uint32_t *b = group_base(MB, ilog2_if_pow2(MB.T), ilog2_if_pow2(MB.tm), t, rest);
+            *a = montmul(*a, *b, p, mont);
+        }
+        __syncthreads();
+        return;
+    }
+    int logLc = logL;
+    for (int i = 0; i + 1 < nst; ++i) {
+        const int b = base + (i < extra ? 1 : 0);
+        run_stage<true, SM>(b, MA, logL, logLc, twf, logT, p, p2);
+        logLc -= b;
+    }
+    wait_b();
+    logLc = logL;
+    for (int i = 0; i + 1 < nst; ++i) {
+        const int b = base + (i < extra ? 1 : 0);
+        run_stage<true, SM>(b, MB, logL, logLc, twf, logT, p, p2);
+        logLc -= b;
+    }
+    const int blast = base + (nst - 1 < extra ? 1 : 0);
+    switch (blast) {
+        case 1: stage_fused_pointwise<2, SM>(MA, MB, logL, twf, twi, logT, p, p2, mont); break;
+        case 2: stage_fused_pointwise<4, SM>(MA, MB, logL, twf, twi, logT, p, p2, mont); break;
+        case 3: stage_fused_pointwise<8, SM>(MA, MB, logL, twf, twi, logT, p, p2, mont); break;
+        default: stage_fused_pointwise<16, SM>(MA, MB, logL, twf, twi, logT, p, p2, mont); break;
+    }
+    logLc = blast;
+    for (int i = nst - 2; i >= 0; --i) {
+        const int b = base + (i < extra ? 1 : 0);
+        logLc += b;
+        run_stage<false, SM>(b, MA, logL, logLc, twi, logT, p, p2);
+    }
+}
+
 // Inverse of ntt_forward up to the factor 2^logL (tw: inverse table): the
 // forward stages replayed backwards.
 template <bool SM = false>
