@@ -1,7 +1,7 @@
 """Benchmark: exact dense Z[y] products on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload large_dense|small_dense|large_all_ones|huge_dense]
+                    [--workload large_dense|small_dense|large_all_ones|huge_dense|batch]
 
 One step is one whole product c = a*b (split, forward 2-D transforms over
 every prime, pointwise products, inverse transforms, CRT, recombination)
@@ -13,6 +13,11 @@ timed steps, outside the events.  Prints ONE JSON line on rank 0.
 --impl reference times the CPU oracle (plain schoolbook definition, all
 host cores) on a bounded sample of the same workload per step and
 extrapolates to products/s.
+
+--workload batch times one ipm_mul_batched call over 4096 products of
+log-uniform degrees in [16, 8192] and bit bounds in [32, 4096] (seed 3) and,
+beside it, the same products as 4096 ipm_mul calls (the plain path without
+batching); `speedup_vs_plain` is their ratio.
 
 Multi-GPU (torchrun): products are independent, so every rank multiplies its
 own pair (weak scaling, no data-path collective); the host-side barrier and
@@ -299,6 +304,71 @@ def recorded_traffic(kernel: str):
     return int(m.group(1)) if m else None
 
 
+def run_batch(args):
+    """The batched workload: products/s of one ipm_mul_batched call (and of
+    the same products one ipm_mul at a time)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1612_05778_gb300 import build as ipm_build
+    ipm_build.build()
+    import paper_1612_05778_gb300 as ipm
+    shapes = W.batch_shapes(seed=3, count=4096)
+    ops = W.batch_operands(shapes, seed=3)
+    plan = ipm.Plan([(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes])
+    dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
+    outs = [plan.empty_output(i) for i in range(len(shapes))]
+    singles = [ipm.Plan((s.na, s.nb, s.bits_a, s.bits_b)) for s in shapes]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms))
+
+    batched = lambda: plan.mul_batched(dev, outs, stream=stream)  # noqa: E731
+
+    def plain():
+        for sp, (da, dan, db, dbn), (c, cn) in zip(singles, dev, outs):
+            sp.mul(da, dan, db, dbn, c, cn, stream=stream)
+
+    for _ in range(args.warmup):
+        batched()
+        plain()
+    torch.cuda.synchronize()
+    plan.sync()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    l0 = ipm.launch_count()
+    ms_b = timed(batched, args.steps)
+    launches = ipm.launch_count() - l0
+    ms_p = timed(plain, max(1, args.steps // 2))
+    clocks = sampler.stop()
+    n = len(shapes)
+    out_bits = sum(s.nc * s.lc * 32 for s in shapes)
+    line = {"metric": METRIC, "value": n / (ms_b / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "output_gbit_s": out_bits / (ms_b / 1e3) / 1e9,
+            "speedup_vs_plain": ms_p / ms_b,
+            "plain": {"ms_per_batch": ms_p, "value": n / (ms_p / 1e3), "path": "one ipm_mul per product"},
+            "config": {"workload": "batch: 4096 products, degrees log-uniform in [16, 8192], bits log-uniform "
+                                   "in [32, 4096], random signs, unbalanced pairs, seed 3",
+                       "products": len(plan.infos), "l2": "flushed between timed steps"},
+            "gpu_launches": int(launches), "launches_per_step": launches / args.steps, "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -463,6 +533,8 @@ def main(argv=None):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 
