@@ -121,6 +121,25 @@ ipm_status ipm_plan(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint32_
 ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint32_t flags,
                        const ipm_params *params);
 
+/*
+ * Candidate plans of one shape for autotuning and cost-model dispatch: every
+ * digit split K that meets the bounds, with the planner's tiles for it and
+ * up to two tile variants (Y2 halved or doubled), each as the override set
+ * that selects it, the plan it yields, and IPM_FEATURES numbers describing
+ * it (log2 of na, nb, bits_a, bits_b, K, M, r, Y, Y2, S, Y1b, transform
+ * points r*Y*2K, middle column length, total input bits; kernel variant
+ * flags).  Writes at most `max` entries and returns how many exist
+ * (negative status on an invalid shape).
+ */
+#define IPM_FEATURES 16
+typedef struct {
+    ipm_params params;
+    ipm_plan_info info;
+    float features[IPM_FEATURES];
+} ipm_candidate;
+int32_t ipm_candidates(const ipm_shape *shape, ipm_candidate *out, int32_t max);
+
+
 /* Plan parameters of shape `index` of a plan. */
 ipm_status ipm_get_info(ipm_plan_t plan, int32_t index, ipm_plan_info *out);
 

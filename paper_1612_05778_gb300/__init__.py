@@ -54,6 +54,13 @@ class PlanInfo(ctypes.Structure):
         return d
 
 
+FEATURES = 16
+
+
+class Candidate(ctypes.Structure):
+    _fields_ = [("params", Params), ("info", PlanInfo), ("features", ctypes.c_float * FEATURES)]
+
+
 class Operands(ctypes.Structure):
     _fields_ = [("a", ctypes.c_void_p), ("a_neg", ctypes.c_void_p), ("b", ctypes.c_void_p),
                 ("b_neg", ctypes.c_void_p), ("c", ctypes.c_void_p), ("c_neg", ctypes.c_void_p)]
@@ -84,6 +91,8 @@ def load_library(path: str | None = None):
     lib.ipm_set_profiling.argtypes = [V, I32]
     lib.ipm_phase_ms.argtypes = [V, ctypes.POINTER(ctypes.c_float), I32]
     lib.ipm_mul_noalloc.argtypes = [ctypes.POINTER(Shape), V, V, V, V, V, V, V]
+    lib.ipm_candidates.argtypes = [ctypes.POINTER(Shape), ctypes.POINTER(Candidate), I32]
+    lib.ipm_candidates.restype = I32
     lib.ipm_strerror.argtypes = [ctypes.c_int]
     lib.ipm_strerror.restype = ctypes.c_char_p
     lib.ipm_launch_count.restype = ctypes.c_int64
@@ -114,6 +123,23 @@ def choose(na: int, nb: int, bits_a: int, bits_b: int, **overrides) -> dict:
     _check(lib.ipm_choose(ctypes.byref(Shape(na - 1, nb - 1, bits_a, bits_b)),
                           ctypes.byref(prm) if prm else None, ctypes.byref(info)), "ipm_choose")
     return info.as_dict()
+
+
+def candidates(na: int, nb: int, bits_a: int, bits_b: int):
+    """Candidate plans of a shape (host only): list of dicts with the override
+    set ('params'), the resulting plan ('info') and the cost-model features."""
+    lib = load_library()
+    shape = Shape(na - 1, nb - 1, bits_a, bits_b)
+    n = lib.ipm_candidates(ctypes.byref(shape), None, 0)
+    if n < 0:
+        raise IpmError(-n, "ipm_candidates")
+    arr = (Candidate * max(n, 1))()
+    lib.ipm_candidates(ctypes.byref(shape), arr, n)
+    out = []
+    for c in arr[:n]:
+        prm = {k: getattr(c.params, k) for k, _ in Params._fields_ if getattr(c.params, k)}
+        out.append({"params": prm, "info": c.info.as_dict(), "features": [float(x) for x in c.features]})
+    return out
 
 
 def launch_count() -> int:
@@ -288,4 +314,4 @@ def to_host(c, c_neg):
 
 
 __all__ = ["Plan", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
-           "IPM_SYNC", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES"]
+           "IPM_SYNC", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES", "candidates"]

@@ -25,6 +25,8 @@ constexpr size_t SMEM_INV_2PERSM = 112 * 1024;
 constexpr int THREADS_FWD = 256;
 constexpr int THREADS_MID = 512;
 constexpr int THREADS_INV = 512;
+constexpr int THREADS_OUTER = 256;
+constexpr int OUTER_TILE_WORDS = 8192;  // outer-pass tile: Y1b rows x W words
 
 // Device error word bits.
 constexpr int ERRBIT_BOUND = 1;      // an input coefficient >= 2^bits
@@ -64,7 +66,7 @@ struct KParams {
     // Y1a i1b) and the twiddle omega_Y1^{i1a k1b}; the middle pass then
     // works on length-Y1a columns.  Y1b = 1: no split.
     int64_t Y1a, Y1b;
-    int32_t logY1a, logY1b, S2, logS2;
+    int32_t logY1a, logY1b, S2, logS2;  // S2: outer-pass tile width in words
     PrimeConst pc[RMAX];
     // Garner: ginv[t][s] = p_s^{-1} mod p_t (s < t), with Shoup quotients.
     uint32_t ginv[RMAX][RMAX];

@@ -252,50 +252,65 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     }
 }
 
-// Outer pass of a split middle transform, on one tile: columns
-// [cs S2, cs S2 + S2) of the rows (pos, i1a + Y1a i1b), i1b < Y1b, prime t,
-// operand op.  Forward: length-Y1b DFT over i1b, then the twiddle
-// omega_Y1^{i1a k1b}.  Inverse: the twiddle's inverse, then the inverse DFT.
+// Outer pass of a split middle transform, on one tile: the Y1b rows
+// (pos, i1a + Y1a i1b), i1b < Y1b, of prime t and operand op, restricted to
+// the W consecutive words [w0, w0 + W) of the flattened (i1a, column) index
+// (a tile may span several i1a).  Forward: a length-Y1b DFT down every word
+// column, then the twiddle omega_Y1^{i1a k1b}.  Inverse: the twiddle's
+// inverse, then the inverse DFT.  Rows are copied with 16-byte cp.async
+// (W, 2K and every row start are multiples of four words).
 template <bool FWD>
-__device__ __forceinline__ void outer_tile(const KParams &P, int cs, int pos, int i1a, int t, int op) {
+__device__ __forceinline__ void outer_tile(const KParams &P, int pos, size_t w0, int t, int op) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int S2 = P.S2, logS2 = P.logS2;
-    const int pitch = S2 + 1;
-    const int twoK = 2 * P.K;
-    const int Y1b = (int)P.Y1b;
-    uint32_t *T = reinterpret_cast<uint32_t *>(smem);                      // [Y1b][pitch]
-    uint2 *tw_rows = reinterpret_cast<uint2 *>(T + ((Y1b * pitch + 1) & ~1));  // Y1b entries
+    const int W = P.S2, logW = P.logS2;
+    const int twoK = 2 * P.K, log2K = P.logK + 1;
+    const int Y1b = (int)P.Y1b, logY1b = P.logY1b;
+    uint32_t *T = reinterpret_cast<uint32_t *>(smem);  // [Y1b][W]
     const PrimeConst &pc = P.pc[t];
     const uint32_t p = pc.p, p2 = pc.p2;
     uint32_t *Zt = P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK;
-    const size_t row0 = (size_t)pos * P.Y1 + i1a;
+    const size_t base = (size_t)pos * P.Y1 * twoK + w0;
     const size_t rstride = (size_t)P.Y1a * twoK;
-    for (int e = threadIdx.x; e < Y1b * S2; e += blockDim.x) {
-        const int ib = e >> logS2, c = e & (S2 - 1);
-        cp_async4(T + ib * pitch + c, Zt + row0 * twoK + ib * rstride + (size_t)cs * S2 + c);
+    const int W4 = W >> 2, logW4 = logW - 2;
+    for (int e = threadIdx.x; e < Y1b * W4; e += blockDim.x) {
+        const int ib = e >> logW4, c4 = e & (W4 - 1);
+        cp_async16(T + ib * W + 4 * c4, Zt + base + ib * rstride + 4 * c4);
     }
     cp_async_commit();
-    const uint2 *tab = FWD ? pc.t1_f : pc.t1_i;
-    for (int q = threadIdx.x; q < Y1b; q += blockDim.x)
-        tw_rows[q] = __ldg(tab + (size_t)i1a * bitrev((uint32_t)q, P.logY1b));
     cp_async_wait<0>();
     __syncthreads();
-    const TileMap m{T, S2, S2, 1, 0, pitch};
+    // twiddle omega_Y1^{+-i1a bitrev(ib)} of element (ib, c)
+    const uint2 *tab = FWD ? pc.t1_f : pc.t1_i;
+    auto tw = [&](int ib, int c) {
+        const uint32_t i1a = (uint32_t)((w0 + (size_t)c) >> log2K);
+        return __ldg(tab + i1a * bitrev((uint32_t)ib, logY1b));
+    };
+    const TileMap m{T, W, W, 1, 0, W};  // W transforms of length Y1b, consecutive threads on consecutive words
     if (FWD) {
-        ntt_forward(m, P.logY1b, pc.t1_f, P.logY1, p, p2);
+        ntt_forward(m, logY1b, pc.t1_f, P.logY1, p, p2);
     } else {
-        for (int e = threadIdx.x; e < Y1b * S2; e += blockDim.x) {
-            const int i = (e >> logS2) * pitch + (e & (S2 - 1));
-            T[i] = shoup(T[i], tw_rows[e >> logS2], p);
+        for (int e = threadIdx.x; e < Y1b * W; e += blockDim.x) {
+            const int ib = e >> logW, c = e & (W - 1);
+            T[e] = shoup(T[e], tw(ib, c), p);
         }
         __syncthreads();
-        ntt_inverse(m, P.logY1b, pc.t1_i, P.logY1, p, p2);
+        ntt_inverse(m, logY1b, pc.t1_i, P.logY1, p, p2);
     }
-    for (int e = threadIdx.x; e < Y1b * S2; e += blockDim.x) {
-        const int ib = e >> logS2, c = e & (S2 - 1);
-        uint32_t v = T[ib * pitch + c];
-        v = FWD ? red(shoup(v, tw_rows[ib], p), p) : red(v, p);
-        Zt[row0 * twoK + ib * rstride + (size_t)cs * S2 + c] = v;
+    for (int e = threadIdx.x; e < Y1b * W4; e += blockDim.x) {
+        const int ib = e >> logW4, c4 = e & (W4 - 1);
+        uint4 v = *reinterpret_cast<const uint4 *>(T + ib * W + 4 * c4);
+        if (FWD) {
+            v.x = red(shoup(v.x, tw(ib, 4 * c4 + 0), p), p);
+            v.y = red(shoup(v.y, tw(ib, 4 * c4 + 1), p), p);
+            v.z = red(shoup(v.z, tw(ib, 4 * c4 + 2), p), p);
+            v.w = red(shoup(v.w, tw(ib, 4 * c4 + 3), p), p);
+        } else {
+            v.x = red(v.x, p);
+            v.y = red(v.y, p);
+            v.z = red(v.z, p);
+            v.w = red(v.w, p);
+        }
+        *reinterpret_cast<uint4 *>(Zt + base + ib * rstride + 4 * c4) = v;
     }
 }
 
@@ -643,16 +658,16 @@ __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant
     mid_tile<SMTW>(P, blockIdx.x, blockIdx.y >> P.logY1b, blockIdx.y & (P.Y1b - 1), blockIdx.z);
 }
 
-// grid: x = (pos * Y1a + i1a) * (2K/S2) + cs; y = 2t + op forward (both
+// grid: x = pos * (Y1a 2K / W) + word block; y = 2t + op forward (both
 // operands), y = t inverse (the product, held in operand A's slab)
 template <bool FWD>
-__global__ void __launch_bounds__(THREADS_MID, 1) k_outer(const __grid_constant__ KParams P) {
-    const int lncs = P.logK + 1 - P.logS2;
-    const int cs = blockIdx.x & ((1 << lncs) - 1);
-    const uint32_t rest = blockIdx.x >> lncs;
+__global__ void __launch_bounds__(THREADS_OUTER) k_outer(const __grid_constant__ KParams P) {
+    const int lnb = P.logY1a + P.logK + 1 - P.logS2;  // word blocks per row: Y1a 2K / W
+    const size_t wb = blockIdx.x & ((1u << lnb) - 1);
+    const int pos = (int)(blockIdx.x >> lnb);
     const int t = FWD ? (int)(blockIdx.y >> 1) : (int)blockIdx.y;
     const int op = FWD ? (int)(blockIdx.y & 1) : 0;
-    outer_tile<FWD>(P, cs, (int)(rest >> P.logY1a), (int)(rest & (P.Y1a - 1)), t, op);
+    outer_tile<FWD>(P, pos, wb << P.logS2, t, op);
 }
 
 template <int NT>
@@ -758,11 +773,11 @@ int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint
 }
 
 int launch_outer(const KParams &kp, size_t smem, bool forward, void *stream) {
-    dim3 grid((unsigned)((2 * kp.K / kp.S2) * kp.Y2 * kp.Y1a), (unsigned)(forward ? 2 * kp.r : kp.r), 1);
+    dim3 grid((unsigned)(kp.Y2 * (kp.Y1a * 2 * kp.K / kp.S2)), (unsigned)(forward ? 2 * kp.r : kp.r), 1);
     if (forward)
-        k_outer<true><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
+        k_outer<true><<<grid, THREADS_OUTER, smem, (cudaStream_t)stream>>>(kp);
     else
-        k_outer<false><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
+        k_outer<false><<<grid, THREADS_OUTER, smem, (cudaStream_t)stream>>>(kp);
     g_launches.fetch_add(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -150,7 +150,7 @@ struct Tiles {
     int32_t S;
     bool mid_tables;
     int64_t Y1b;   // outer split of the middle transform (1 = none)
-    int32_t S2;    // outer pass column slice
+    int32_t S2;    // outer pass tile width W (words)
     size_t smem_fwd, smem_mid, smem_inv, smem_outer;
 };
 
@@ -167,8 +167,12 @@ size_t inv_smem(int64_t Y2, int K, int r, int lc) {
 size_t mid_smem(int64_t Y1, int S, bool tables) {
     return ((size_t)2 * Y1 * (S + 1) + 16) * 4 + (tables ? (size_t)2 * Y1 * 8 : 0);
 }
-// outer pass: one operand's Y1b x S2 tile plus its Y1b row twiddles
-size_t outer_smem(int64_t Y1b, int S2) { return (size_t)Y1b * (S2 + 1) * 4 + (size_t)Y1b * 8; }
+// outer pass: Y1b rows x W consecutive words of one operand (W a power of
+// two >= 4, about OUTER_TILE_WORDS words per tile)
+int64_t outer_width(int64_t Y1a, int K, int64_t Y1b) {
+    return std::min<int64_t>(Y1a * 2 * K, std::max<int64_t>(4, OUTER_TILE_WORDS / Y1b));
+}
+size_t outer_smem(int64_t Y1b, int64_t W) { return (size_t)Y1b * (size_t)W * 4; }
 
 // Tile shapes: Y2 rows per forward/inverse tile, S columns per middle tile
 // (Y1 = Y / Y2 is the middle pass's column length).  Hard limit: every pass
@@ -214,15 +218,10 @@ bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force
             }
             if (s_force && (s_force > 2 * K || (s_force & (s_force - 1)))) S = 0;
             if (S == 0) continue;
-            int S2 = 0;
-            if (Y1b > 1) {
-                for (int s = std::min(2 * K, 32); s >= 1; s >>= 1)
-                    if (outer_smem(Y1b, s) <= SMEM_MID_MAX) { S2 = s; break; }
-                if (S2 == 0) continue;
-            }
+            const int64_t S2 = Y1b > 1 ? outer_width(Y1a, K, Y1b) : 0;
+            if (Y1b > 1 && outer_smem(Y1b, S2) > SMEM_MID_MAX) continue;
             const double score = (S >= 8 || S == 2 * K ? 0 : 8) + (iv <= SMEM_INV_2PERSM ? 0 : 4) +
                                  (fw <= SMEM_FWD_3PERSM ? 0 : 2) + (tab ? 0 : 1) + (Y1b > 1 ? 3 : 0) +
-                                 (Y1b > 1 && S2 < 8 && S2 < 2 * K ? 8 : 0) +
                                  0.1 * std::abs(ilog2((uint64_t)Y2) - ilog2((uint64_t)target));
             if (!found || score < best) {
                 found = true;
@@ -231,7 +230,7 @@ bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force
                 t.S = S;
                 t.mid_tables = tab;
                 t.Y1b = Y1b;
-                t.S2 = S2 ? S2 : 1;
+                t.S2 = S2 ? (int32_t)S2 : 1;
                 t.smem_fwd = fw;
                 t.smem_mid = mid_smem(Y1a, S, tab);
                 t.smem_inv = iv;
@@ -427,6 +426,68 @@ void build_tables(ShapePlan &sp, uint2 *tab) {
 }
 
 }  // namespace ipm
+
+namespace ipm {
+
+void candidate_features(const ipm_shape &sh, const ShapePlan &sp, float *f) {
+    const ipm_plan_info &I = sp.info;
+    auto lg = [](double x) { return (float)std::log2(std::max(1.0, x)); };
+    f[0] = lg((double)I.na);
+    f[1] = lg((double)I.nb);
+    f[2] = lg((double)sh.bits_a);
+    f[3] = lg((double)sh.bits_b);
+    f[4] = lg((double)I.K);
+    f[5] = (float)I.M / 32.0f;
+    f[6] = (float)I.r;
+    f[7] = lg((double)I.Y);
+    f[8] = lg((double)I.Y2);
+    f[9] = lg((double)I.S);
+    f[10] = lg((double)I.Y1b);
+    f[11] = lg((double)I.r * (double)I.Y * 2.0 * I.K);
+    f[12] = lg((double)sp.kp.Y1a);
+    f[13] = lg((double)I.na * sh.bits_a + (double)I.nb * sh.bits_b);
+    f[14] = sp.smem_fwd <= SMEM_FWD_3PERSM ? 1.0f : 0.0f;
+    f[15] = sp.smem_inv <= SMEM_INV_2PERSM ? 1.0f : 0.0f;
+}
+
+}  // namespace ipm
+
+extern "C" int32_t ipm_candidates(const ipm_shape *shape, ipm_candidate *out, int32_t max) {
+    if (!shape || max < 0 || (max > 0 && !out)) return -(int32_t)IPM_ERR_ARG;
+    ipm::ShapePlan base;
+    ipm_status st = ipm::choose_plan(*shape, nullptr, base);
+    if (st != IPM_OK) return -(int32_t)st;
+    std::vector<std::pair<ipm_params, ipm::ShapePlan>> found;
+    auto add = [&](const ipm_params &prm) {
+        ipm::ShapePlan sp;
+        if (ipm::choose_plan(*shape, &prm, sp) != IPM_OK) return;
+        for (auto &f : found) {
+            const ipm_plan_info &a = f.second.info, &b = sp.info;
+            if (a.K == b.K && a.M == b.M && a.r == b.r && a.Y2 == b.Y2 && a.S == b.S && a.Y1b == b.Y1b) return;
+        }
+        found.emplace_back(prm, sp);
+    };
+    for (int logK = 1; logK <= ipm::KMAX_LOG2; ++logK) {
+        ipm_params prm{};
+        prm.K = 1 << logK;
+        ipm::ShapePlan sp;
+        if (ipm::choose_plan(*shape, &prm, sp) != IPM_OK) continue;
+        add(prm);
+        for (int64_t y2 : {sp.info.Y2 / 2, sp.info.Y2 * 2}) {
+            if (y2 < 1) continue;
+            ipm_params v = prm;
+            v.y2 = (int32_t)y2;
+            add(v);
+        }
+    }
+    const int32_t n = (int32_t)found.size();
+    for (int32_t i = 0; i < n && i < max; ++i) {
+        out[i].params = found[(size_t)i].first;
+        out[i].info = found[(size_t)i].second.info;
+        ipm::candidate_features(*shape, found[(size_t)i].second, out[i].features);
+    }
+    return n;
+}
 
 extern "C" ipm_status ipm_choose(const ipm_shape *shape, const ipm_params *params,
                                  ipm_plan_info *out) {
