@@ -14,10 +14,16 @@ timed steps, outside the events.  Prints ONE JSON line on rank 0.
 host cores) on a bounded sample of the same workload per step and
 extrapolates to products/s.
 
+The timed plan is the one the learned dispatch picks (IPM_COSTMODEL with
+the committed GB300 cost model); `--plain` times the analytic planner's
+plan instead.  When the two differ, the plain plan is timed beside it on the
+same inputs and `speedup_vs_plain` is the ratio (1 when they coincide).
+
 --workload batch times one ipm_mul_batched call over 4096 products of
-log-uniform degrees in [16, 8192] and bit bounds in [32, 4096] (seed 3) and,
-beside it, the same products as 4096 ipm_mul calls (the plain path without
-batching); `speedup_vs_plain` is their ratio.
+log-uniform degrees in [16, 8192] and bit bounds in [32, 4096] (seed 3) with
+the learned dispatch and, beside it, the same batch with the analytic
+planner and the same products as 4096 ipm_mul calls (the plain path);
+`speedup_vs_plain` is the ratio to the plain path.
 
 Multi-GPU (torchrun): products are independent, so every rank multiplies its
 own pair (weak scaling, no data-path collective); the host-side barrier and
@@ -314,7 +320,14 @@ def run_batch(args):
     import paper_1612_05778_gb300 as ipm
     shapes = W.batch_shapes(seed=3, count=4096)
     ops = W.batch_operands(shapes, seed=3)
-    plan = ipm.Plan([(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes])
+    tuples = [(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes]
+    flags = 0
+    if not args.plain:
+        from paper_1612_05778_gb300 import costmodel as cmod
+        cmod.install()
+        flags = ipm.IPM_COSTMODEL
+    plan = ipm.Plan(tuples, flags=flags)            # the chosen form
+    plan_planner = ipm.Plan(tuples)                 # batched, analytic planner
     dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
     outs = [plan.empty_output(i) for i in range(len(shapes))]
     singles = [ipm.Plan((s.na, s.nb, s.bits_a, s.bits_b)) for s in shapes]
@@ -335,6 +348,7 @@ def run_batch(args):
         return float(np.mean(ms))
 
     batched = lambda: plan.mul_batched(dev, outs, stream=stream)  # noqa: E731
+    batched_planner = lambda: plan_planner.mul_batched(dev, outs, stream=stream)  # noqa: E731
 
     def plain():
         for sp, (da, dan, db, dbn), (c, cn) in zip(singles, dev, outs):
@@ -342,16 +356,22 @@ def run_batch(args):
 
     for _ in range(args.warmup):
         batched()
+        batched_planner()
         plain()
     torch.cuda.synchronize()
     plan.sync()
+    plan_planner.sync()
     sampler = ClockSampler(0)
     sampler.start()
     time.sleep(0.3)
     l0 = ipm.launch_count()
     ms_b = timed(batched, args.steps)
     launches = ipm.launch_count() - l0
+    ms_bp = timed(batched_planner, max(1, args.steps // 2))
     ms_p = timed(plain, max(1, args.steps // 2))
+    plan_planner.sync()
+    changed = sum(any(a[k] != b[k] for k in ("K", "M", "r", "Y2", "S", "Y1b"))
+                  for a, b in zip(plan.infos, plan_planner.infos))
     clocks = sampler.stop()
     n = len(shapes)
     out_bits = sum(s.nc * s.lc * 32 for s in shapes)
@@ -360,7 +380,12 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "output_gbit_s": out_bits / (ms_b / 1e3) / 1e9,
             "speedup_vs_plain": ms_p / ms_b,
-            "plain": {"ms_per_batch": ms_p, "value": n / (ms_p / 1e3), "path": "one ipm_mul per product"},
+            "plain": {"ms_per_batch": ms_p, "value": n / (ms_p / 1e3),
+                      "path": "one ipm_mul per product, analytic planner"},
+            "batched_planner": {"ms_per_batch": ms_bp, "value": n / (ms_bp / 1e3),
+                                "path": "one ipm_mul_batched call, analytic planner"},
+            "dispatch": {"flags": "IPM_COSTMODEL" if flags else "none (--plain)",
+                         "products_with_another_plan": int(changed)},
             "config": {"workload": "batch: 4096 products, degrees log-uniform in [16, 8192], bits log-uniform "
                                    "in [32, 4096], random signs, unbalanced pairs, seed 3",
                        "products": len(plan.infos), "l2": "flushed between timed steps"},
@@ -382,8 +407,21 @@ def run_ours(args):
     import paper_1612_05778_gb300 as ipm
 
     name, sh, a, b = workload(args.workload)
-    plan = ipm.Plan((sh.na, sh.nb, sh.bits_a, sh.bits_b))
+    shape = (sh.na, sh.nb, sh.bits_a, sh.bits_b)
+    # the chosen form: the plan the learned dispatch picks (committed GB300
+    # cost model); --plain forces the analytic planner's plan
+    flags = 0
+    dispatch = {"source": "planner (--plain)", "params": {}}
+    if not args.plain:
+        from paper_1612_05778_gb300 import costmodel as cmod
+        cmod.install()
+        flags = ipm.IPM_COSTMODEL
+        prm, src = ipm.dispatch(*shape)
+        dispatch = {"source": src, "params": prm}
+    plan = ipm.Plan(shape, flags=flags)
     info = plan.info
+    plain_plan = ipm.Plan(shape)
+    same_plan = all(plain_plan.info[k] == info[k] for k in ("K", "M", "r", "Y2", "S", "Y1b"))
     da, dan = ipm.to_device(*a)
     db, dbn = ipm.to_device(*b)
     c, cn = plan.empty_output()
@@ -425,6 +463,29 @@ def run_ours(args):
     clocks = sampler.stop()
     plan.set_profiling(False)
     plan.sync()
+
+    # the plain path (analytic planner) on the same inputs, when it differs
+    plain_ms = None
+    if not same_plan:
+        c2, cn2 = plain_plan.empty_output()
+        for _ in range(args.warmup):
+            plain_plan.mul(da, dan, db, dbn, c2, cn2)
+        pm = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plain_plan.mul(da, dan, db, dbn, c2, cn2, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            pm.append(e0.elapsed_time(e1))
+        plain_plan.sync()
+        if not (torch.equal(c, c2) and torch.equal(cn, cn2)):
+            raise SystemExit("chosen and plain plans disagree")
+        plain_ms = float(np.mean(pm))
+        del c2, cn2
+    plain_plan.close()
 
     local_ms = float(np.sum(step_ms))
     total_ms = max_over_ranks(dist, local_ms, dev)
@@ -495,12 +556,16 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "output_gbit_s": out_bits * value / 1e9,
-        "speedup_vs_plain": 1.0,
+        "speedup_vs_plain": (plain_ms / (local_ms / args.steps)) if plain_ms else 1.0,
+        "plain": ({"ms_per_step": plain_ms, "path": "analytic planner's plan"} if plain_ms else
+                  {"path": "the analytic planner picks the same plan: one path, ratio 1"}),
         "config": {"workload": name, "na": sh.na, "nb": sh.nb, "bits": sh.bits_a, "lc": sh.lc,
-                   "plan": {k: info[k] for k in ("K", "M", "N", "r", "Y", "Y1", "Y2", "S")},
+                   "plan": {k: info[k] for k in ("K", "M", "N", "r", "Y", "Y1", "Y2", "S", "Y1b")},
+                   "dispatch": dispatch,
                    "primes": info["primes"], "parallelism": "replicas (one product per GPU)",
                    "l2": "flushed between timed steps (512 MiB write, outside the events)",
-                   "path": "plain 2-D NTT (Shoup butterflies), 3 launches per product"},
+                   "path": "2-D NTT (Shoup butterflies), %d launches per product" % (
+                       3 + (2 if info["Y1b"] > 1 else 0))},
         "roofline": roofline,
         "passes": passes,
         "cpu_baseline": cpu,
@@ -526,6 +591,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="large_dense")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--plain", action="store_true",
+                    help="the plain path: analytic planner only, no learned dispatch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args(argv)

@@ -67,6 +67,8 @@ typedef enum {
 
 /* Plan flags. */
 #define IPM_SYNC 1u           /* calls synchronise and return device errors */
+#define IPM_COSTMODEL 2u      /* learned dispatch picks each shape's plan (see
+                                 ipm_set_cost_model); ignored with params */
 
 /* One product shape: a has deg_a+1 coefficients with |a_i| < 2^bits_a. */
 typedef struct {
@@ -139,6 +141,58 @@ typedef struct {
 } ipm_candidate;
 int32_t ipm_candidates(const ipm_shape *shape, ipm_candidate *out, int32_t max);
 
+/*
+ * Learned plan dispatch (no counterpart in the paper, whose DetermineBase,
+ * §2.4, reads the split from a precomputed table).  A multilayer perceptron
+ * IPM_FEATURES -> 32 -> 32 -> 1 with ReLU maps a candidate's features to
+ * its predicted run time.  With the plan flag IPM_COSTMODEL (and params
+ * NULL), ipm_plan / ipm_plan_ex take for each shape (1) the measured best
+ * plan from the tuning table (ipm_set_tuned) when the shape is in it, else
+ * (2) the candidate with the smallest predicted time under the installed
+ * model (ipm_set_cost_model), else (3) the analytic planner.  Every
+ * candidate computes the same exact product: the model chooses speed only.
+ *
+ * Model: IPM_MLP_FLOATS host floats: feature means [F], inverse standard
+ * deviations [F] (0 for a constant feature), target mean, target standard
+ * deviation, then the IPM_MLP_PARAMS parameters W1[32][F], b1[32],
+ * W2[32][32], b2[32], w3[32], b3 (F = IPM_FEATURES, row-major).  The network
+ * sees standardised features and predicts the standardised target.
+ *
+ * ipm_mlp_train: n >= 2 host samples X[n][F] (row-major) with targets y[n]:
+ *   computes the standardisation, draws Glorot-uniform weights from `seed`
+ *   (splitmix64; biases zero), runs `epochs` full-batch Adam steps
+ *   (learning rate lr, beta1 0.9, beta2 0.999, on the mean loss) on the GPU
+ *   and writes the model to `model`, and the final mean of 1/2 (o - t)^2
+ *   to *final_loss (may be NULL).
+ * ipm_mlp_grad: for a host model, the sum over samples of 1/2 (o - t)^2
+ *   (*loss) and its gradient with respect to the IPM_MLP_PARAMS parameters
+ *   (grad[], host), from the GPU kernel that training uses.
+ * ipm_mlp_predict: out[i] = the model's prediction for X[i], in target
+ *   units (host arrays; n may be 0).
+ * ipm_set_cost_model: copy `model` (nfloats = IPM_MLP_FLOATS) for
+ *   IPM_COSTMODEL; NULL uninstalls it.
+ * ipm_set_tuned: replace the tuning table by n (shape, params) pairs
+ *   (n = 0 clears it); if a pair does not plan, its status is returned and
+ *   the table is left unchanged.
+ * ipm_dispatch: the params IPM_COSTMODEL gives `shape` (all zero: the
+ *   analytic planner) and their source (*source: 0 planner, 1 table,
+ *   2 model; may be NULL).
+ * These run on the current device, allocate their own scratch and wait for
+ * it: not for use during stream capture.  Float sums in the gradient are
+ * unordered, so trained weights may differ in their last bits between runs.
+ */
+#define IPM_MLP_HIDDEN 32
+#define IPM_MLP_PARAMS \
+    (IPM_MLP_HIDDEN * IPM_FEATURES + IPM_MLP_HIDDEN * IPM_MLP_HIDDEN + 3 * IPM_MLP_HIDDEN + 1)
+#define IPM_MLP_FLOATS (2 * IPM_FEATURES + 2 + IPM_MLP_PARAMS)
+ipm_status ipm_mlp_train(const float *X, const float *y, int32_t n, int32_t epochs, float lr,
+                         uint64_t seed, float *model, float *final_loss);
+ipm_status ipm_mlp_grad(const float *model, const float *X, const float *y, int32_t n,
+                        float *grad, float *loss);
+ipm_status ipm_mlp_predict(const float *model, const float *X, int32_t n, float *out);
+ipm_status ipm_set_cost_model(const float *model, int32_t nfloats);
+ipm_status ipm_set_tuned(const ipm_shape *shapes, const ipm_params *params, int32_t n);
+ipm_status ipm_dispatch(const ipm_shape *shape, ipm_params *out, int32_t *source);
 
 /* Plan parameters of shape `index` of a plan. */
 ipm_status ipm_get_info(ipm_plan_t plan, int32_t index, ipm_plan_info *out);

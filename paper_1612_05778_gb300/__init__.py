@@ -17,6 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libipm.so")
 
 IPM_SYNC = 1
+IPM_COSTMODEL = 2
 
 STATUS = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_BOUND", 3: "IPM_ERR_NOMEM",
           4: "IPM_ERR_CUDA", 5: "IPM_ERR_TIMEOUT", 6: "IPM_ERR_UNSUPPORTED"}
@@ -55,6 +56,9 @@ class PlanInfo(ctypes.Structure):
 
 
 FEATURES = 16
+MLP_HIDDEN = 32
+MLP_PARAMS = MLP_HIDDEN * FEATURES + MLP_HIDDEN * MLP_HIDDEN + 3 * MLP_HIDDEN + 1
+MLP_FLOATS = 2 * FEATURES + 2 + MLP_PARAMS
 
 
 class Candidate(ctypes.Structure):
@@ -93,12 +97,20 @@ def load_library(path: str | None = None):
     lib.ipm_mul_noalloc.argtypes = [ctypes.POINTER(Shape), V, V, V, V, V, V, V]
     lib.ipm_candidates.argtypes = [ctypes.POINTER(Shape), ctypes.POINTER(Candidate), I32]
     lib.ipm_candidates.restype = I32
+    F32P = ctypes.POINTER(ctypes.c_float)
+    lib.ipm_mlp_train.argtypes = [F32P, F32P, I32, I32, ctypes.c_float, ctypes.c_uint64, F32P, F32P]
+    lib.ipm_mlp_grad.argtypes = [F32P, F32P, F32P, I32, F32P, F32P]
+    lib.ipm_mlp_predict.argtypes = [F32P, F32P, I32, F32P]
+    lib.ipm_set_cost_model.argtypes = [F32P, I32]
+    lib.ipm_set_tuned.argtypes = [ctypes.POINTER(Shape), ctypes.POINTER(Params), I32]
+    lib.ipm_dispatch.argtypes = [ctypes.POINTER(Shape), ctypes.POINTER(Params), ctypes.POINTER(I32)]
     lib.ipm_strerror.argtypes = [ctypes.c_int]
     lib.ipm_strerror.restype = ctypes.c_char_p
     lib.ipm_launch_count.restype = ctypes.c_int64
     for name in ("ipm_choose", "ipm_plan", "ipm_plan_ex", "ipm_get_info", "ipm_mul", "ipm_mul_host",
                  "ipm_mul_batched", "ipm_sync", "ipm_destroy", "ipm_set_profiling", "ipm_phase_ms",
-                 "ipm_mul_noalloc"):
+                 "ipm_mul_noalloc", "ipm_mlp_train", "ipm_mlp_grad", "ipm_mlp_predict",
+                 "ipm_set_cost_model", "ipm_set_tuned", "ipm_dispatch"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -140,6 +152,85 @@ def candidates(na: int, nb: int, bits_a: int, bits_b: int):
         prm = {k: getattr(c.params, k) for k, _ in Params._fields_ if getattr(c.params, k)}
         out.append({"params": prm, "info": c.info.as_dict(), "features": [float(x) for x in c.features]})
     return out
+
+
+def _f32(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if n is not None and a.size != n:
+        raise ValueError("expected %d floats, got %d" % (n, a.size))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def mlp_train(X, y, epochs: int = 3000, lr: float = 3e-3, seed: int = 0):
+    """Train the cost-model network on the GPU: returns (model, final mean loss)."""
+    lib = load_library()
+    X, xp = _f32(X)
+    y, yp = _f32(y)
+    n = int(y.size)
+    if X.shape != (n, FEATURES):
+        raise ValueError("X must be (n, %d)" % FEATURES)
+    model = np.zeros(MLP_FLOATS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(lib.ipm_mlp_train(xp, yp, n, epochs, lr, seed,
+                             model.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)),
+           "ipm_mlp_train")
+    return model, float(loss.value)
+
+
+def mlp_grad(model, X, y):
+    """(summed loss, gradient over the MLP_PARAMS parameters) from the GPU kernel."""
+    lib = load_library()
+    model, mp = _f32(model, MLP_FLOATS)
+    X, xp = _f32(X)
+    y, yp = _f32(y)
+    g = np.zeros(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(lib.ipm_mlp_grad(mp, xp, yp, int(y.size), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                            ctypes.byref(loss)), "ipm_mlp_grad")
+    return float(loss.value), g
+
+
+def mlp_predict(model, X):
+    """Predictions of the network for the rows of X (GPU kernel)."""
+    lib = load_library()
+    model, mp = _f32(model, MLP_FLOATS)
+    X, xp = _f32(X)
+    n = X.size // FEATURES
+    out = np.zeros(n, dtype=np.float32)
+    _check(lib.ipm_mlp_predict(mp, xp, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+           "ipm_mlp_predict")
+    return out
+
+
+def set_cost_model(model):
+    """Install a model for IPM_COSTMODEL plans (None uninstalls)."""
+    lib = load_library()
+    if model is None:
+        _check(lib.ipm_set_cost_model(None, 0), "ipm_set_cost_model")
+        return
+    model, mp = _f32(model, MLP_FLOATS)
+    _check(lib.ipm_set_cost_model(mp, MLP_FLOATS), "ipm_set_cost_model")
+
+
+def set_tuned(entries):
+    """Replace the tuning table: entries = [((na, nb, bits_a, bits_b), params dict), ...]."""
+    lib = load_library()
+    n = len(entries)
+    shapes = (Shape * max(n, 1))(*[Shape(na - 1, nb - 1, ba, bb) for (na, nb, ba, bb), _ in entries])
+    prms = (Params * max(n, 1))(*[Params(*(p.get(k, 0) for k, _ in Params._fields_)) for _, p in entries])
+    _check(lib.ipm_set_tuned(shapes, prms, n), "ipm_set_tuned")
+
+
+def dispatch(na: int, nb: int, bits_a: int, bits_b: int):
+    """(params dict, source) that IPM_COSTMODEL gives a shape; source is
+    'planner', 'table' or 'model'."""
+    lib = load_library()
+    prm = Params()
+    src = ctypes.c_int32()
+    _check(lib.ipm_dispatch(ctypes.byref(Shape(na - 1, nb - 1, bits_a, bits_b)), ctypes.byref(prm),
+                            ctypes.byref(src)), "ipm_dispatch")
+    return ({k: getattr(prm, k) for k, _ in Params._fields_ if getattr(prm, k)},
+            ("planner", "table", "model")[src.value])
 
 
 def launch_count() -> int:
@@ -314,4 +405,5 @@ def to_host(c, c_neg):
 
 
 __all__ = ["Plan", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
-           "IPM_SYNC", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES", "candidates"]
+           "IPM_SYNC", "IPM_COSTMODEL", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES", "candidates",
+           "mlp_train", "mlp_grad", "mlp_predict", "set_cost_model", "set_tuned", "dispatch"]

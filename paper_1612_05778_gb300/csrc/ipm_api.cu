@@ -217,8 +217,16 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
     if (set_kernel_attributes()) { free_plan(plan); return IPM_ERR_CUDA; }
     plan->shapes.resize((size_t)n);
     size_t zmax = 0;
+    std::vector<ipm_params> learned;
+    if ((flags & IPM_COSTMODEL) && !params) {
+        learned.resize((size_t)n);
+        std::vector<int32_t> src((size_t)n);
+        ipm_status st = dispatch_params(shapes, n, learned.data(), src.data());
+        if (st != IPM_OK) { free_plan(plan); return st; }
+    }
     for (int32_t i = 0; i < n; ++i) {
-        ipm_status st = choose_plan(shapes[i], params, plan->shapes[(size_t)i]);
+        ipm_status st = choose_plan(shapes[i], learned.empty() ? params : &learned[(size_t)i],
+                                    plan->shapes[(size_t)i]);
         if (st != IPM_OK) { free_plan(plan); return st; }
         zmax = std::max(zmax, plan->shapes[(size_t)i].z_words);
     }

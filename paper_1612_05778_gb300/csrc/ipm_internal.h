@@ -90,6 +90,10 @@ struct ShapePlan {
 // Planner (host only).  Fills sp (minus device pointers) or returns an error.
 ipm_status choose_plan(const ipm_shape &shape, const ipm_params *params, ShapePlan &sp);
 
+// Learned dispatch for n shapes (ipm_mlp.cu): params per shape and their
+// source (0 planner: params all zero, 1 tuning table, 2 model).
+ipm_status dispatch_params(const ipm_shape *shapes, int32_t n, ipm_params *out, int32_t *src);
+
 // Builds the per-prime tables for sp into host memory `tab` (r blocks of
 // sp.table_words uint2 entries) and fills the scalar constants of sp.kp.
 void build_tables(ShapePlan &sp, uint2 *tab);

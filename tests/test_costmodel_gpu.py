@@ -1,0 +1,146 @@
+"""GPU tests of the learned plan dispatch.
+
+* The CUDA gradient, loss and forward pass of the cost-model network agree
+  with the float64 CPU reference (oracle/mlp.py, itself pinned to finite
+  differences) on a batch that spans several blocks and a ragged tail.
+* GPU training fits a known smooth function.
+* Plans chosen by the model (or the tuning table) give bit-identical
+  products to the analytic planner's plan.
+* Trained on the committed GB300 sweep's training points, the model's regret
+  on the held-out points is no worse than the analytic planner's: what the
+  network gains over the method without it.
+"""
+import numpy as np
+import pytest
+
+import paper_1612_05778_gb300 as ipm
+from oracle import mlp as omlp
+from paper_1612_05778_gb300 import costmodel as cm
+
+pytestmark = pytest.mark.gpu
+
+
+_DIST = np.random.default_rng(100)
+_SCALE = _DIST.uniform(0.5, 3, omlp.F)
+_SHIFT = _DIST.uniform(-2, 2, omlp.F)
+
+
+def _data(rng, n):
+    """Samples of one fixed input distribution and a smooth target."""
+    X = rng.normal(size=(n, omlp.F)) * _SCALE + _SHIFT
+    y = X[:, 0] - 0.5 * X[:, 3] + np.sin(X[:, 5]) + 0.3 * np.abs(X[:, 7])
+    return X.astype(np.float32), y.astype(np.float32)
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (31, 1), (1000, 2), (4099, 3)])
+def test_gradient_matches_cpu_reference(n, seed):
+    rng = np.random.default_rng(seed)
+    X, y = _data(rng, n)
+    model = omlp.random_model(rng, X, y).astype(np.float32)
+    L_ref, g_ref = omlp.grad(model.astype(np.float64), X.astype(np.float64), y.astype(np.float64))
+    L, g = ipm.mlp_grad(model, X, y)
+    assert L == pytest.approx(L_ref, rel=1e-4, abs=1e-5)
+    scale = np.max(np.abs(g_ref))
+    np.testing.assert_allclose(g, g_ref, rtol=1e-3, atol=2e-5 * scale)
+
+
+def test_forward_matches_cpu_reference():
+    rng = np.random.default_rng(11)
+    X, y = _data(rng, 777)
+    model = omlp.random_model(rng, X, y).astype(np.float32)
+    ref = omlp.predict(model.astype(np.float64), X.astype(np.float64))
+    got = ipm.mlp_predict(model, X)
+    np.testing.assert_allclose(got, ref, rtol=1e-4, atol=1e-4 * np.max(np.abs(ref)))
+    assert ipm.mlp_predict(model, X[:0]).size == 0
+
+
+def test_training_fits_a_smooth_function():
+    rng = np.random.default_rng(12)
+    X, y = _data(rng, 2000)
+    model, loss = ipm.mlp_train(X, y, epochs=3000, lr=3e-3, seed=1)
+    assert np.all(np.isfinite(model))
+    assert loss < 0.01                       # mean 1/2 (o - t)^2 on standardised targets
+    Xt, yt = _data(np.random.default_rng(13), 500)
+    err = ipm.mlp_predict(model, Xt) - yt
+    assert np.sqrt(np.mean(err ** 2)) < 0.2 * np.std(yt)
+    # the returned loss is the one the gradient kernel measures
+    L, _ = ipm.mlp_grad(model, X, y)
+    assert L / len(y) == pytest.approx(loss, rel=1e-3)
+
+
+def test_training_rejects_bad_arguments():
+    lib = ipm.load_library()
+    assert lib.ipm_mlp_train(None, None, 10, 1, 1e-3, 0, None, None) == 1
+    with pytest.raises(ValueError):
+        ipm.set_cost_model(np.zeros(10, dtype=np.float32))
+
+
+@pytest.fixture
+def committed_model():
+    model, _ = cm.load_model()
+    yield model
+    ipm.set_cost_model(None)
+    ipm.set_tuned([])
+
+
+def _product(shape, flags, seed):
+    import workloads as W
+    import torch
+    na, nb, ba, bb = shape
+    rng = np.random.default_rng(seed)
+    A = W.random_poly(rng, na, ba)
+    B = W.random_poly(rng, nb, bb)
+    plan = ipm.Plan(shape, flags=flags)
+    a, an = ipm.to_device(*A)
+    b, bn = ipm.to_device(*B)
+    c, cn = plan.empty_output()
+    plan.mul(a, an, b, bn, c, cn)
+    plan.sync()
+    torch.cuda.synchronize()
+    info = plan.info
+    plan.close()
+    return ipm.to_host(c, cn), info
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 32, 32), (1024, 1024, 2048, 2048), (4096, 4096, 64, 64),
+                                   (500, 3000, 100, 1000)])
+def test_model_dispatch_is_exact(committed_model, shape):
+    ipm.set_cost_model(committed_model)
+    prm, src = ipm.dispatch(*shape)
+    assert src == "model"
+    (c1, s1), info1 = _product(shape, ipm.IPM_COSTMODEL, 7)
+    (c0, s0), _ = _product(shape, 0, 7)
+    for k, v in prm.items():
+        key = {"y2": "Y2", "s": "S", "y1b": "Y1b"}.get(k, k)
+        assert info1[key] == v
+    assert np.array_equal(c0, c1) and np.array_equal(s0, s1)
+
+
+def test_tuning_table_takes_precedence(committed_model):
+    shape = (2048, 2048, 512, 512)
+    ipm.set_cost_model(committed_model)
+    cands = ipm.candidates(*shape)
+    pick = cands[-1]["params"]
+    ipm.set_tuned([(shape, pick)])
+    prm, src = ipm.dispatch(*shape)
+    assert src == "table" and prm == pick
+    (c1, s1), info = _product(shape, ipm.IPM_COSTMODEL, 8)
+    assert info["K"] == cands[-1]["info"]["K"]
+    (c0, s0), _ = _product(shape, 0, 8)
+    assert np.array_equal(c0, c1) and np.array_equal(s0, s1)
+    ipm.set_tuned([])
+    ipm.set_cost_model(None)
+    assert ipm.dispatch(*shape) == ({}, "planner")
+
+
+def test_trained_model_beats_planner_on_held_out_points():
+    sweep = cm.load_sweep()
+    train, held = cm.split_points(sweep["points"])
+    model, loss = cm.train(train, epochs=4000, lr=1e-3, seed=0)
+    ev = cm.evaluate(model, held)
+    print("held-out regret: model %.4f (max %.3f, optimal %.0f%%), planner %.4f (max %.3f, optimal %.0f%%)" % (
+        ev["model"]["mean"], ev["model"]["max"], 100 * ev["model"]["optimal_fraction"],
+        ev["planner"]["mean"], ev["planner"]["max"], 100 * ev["planner"]["optimal_fraction"]))
+    assert ev["points"] == len(held) >= 40
+    assert ev["model"]["geomean_slowdown"] <= ev["planner"]["geomean_slowdown"]
+    assert ev["model"]["mean"] <= ev["planner"]["mean"]
