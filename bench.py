@@ -370,7 +370,7 @@ def run_batch(args):
     ms_bp = timed(batched_planner, max(1, args.steps // 2))
     ms_p = timed(plain, max(1, args.steps // 2))
     plan_planner.sync()
-    changed = sum(any(a[k] != b[k] for k in ("K", "M", "r", "Y2", "S", "Y1b"))
+    changed = sum(any(a[k] != b[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron"))
                   for a, b in zip(plan.infos, plan_planner.infos))
     clocks = sampler.stop()
     n = len(shapes)
@@ -421,7 +421,7 @@ def run_ours(args):
     plan = ipm.Plan(shape, flags=flags)
     info = plan.info
     plain_plan = ipm.Plan(shape)
-    same_plan = all(plain_plan.info[k] == info[k] for k in ("K", "M", "r", "Y2", "S", "Y1b"))
+    same_plan = all(plain_plan.info[k] == info[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron"))
     da, dan = ipm.to_device(*a)
     db, dbn = ipm.to_device(*b)
     c, cn = plan.empty_output()
@@ -560,7 +560,7 @@ def run_ours(args):
         "plain": ({"ms_per_step": plain_ms, "path": "analytic planner's plan"} if plain_ms else
                   {"path": "the analytic planner picks the same plan: one path, ratio 1"}),
         "config": {"workload": name, "na": sh.na, "nb": sh.nb, "bits": sh.bits_a, "lc": sh.lc,
-                   "plan": {k: info[k] for k in ("K", "M", "N", "r", "Y", "Y1", "Y2", "S", "Y1b")},
+                   "plan": {k: info[k] for k in ("K", "M", "N", "r", "Y", "Y1", "Y2", "S", "Y1b", "kron")},
                    "dispatch": dispatch,
                    "primes": info["primes"], "parallelism": "replicas (one product per GPU)",
                    "l2": "flushed between timed steps (512 MiB write, outside the events)",

@@ -85,9 +85,15 @@ typedef struct {
  *   y2: rows per forward/inverse tile (power of two dividing Y)
  *   s : columns per middle-pass tile (power of two dividing 2K)
  *   y1b: split the middle transform in two (power of two > 1 dividing Y/y2)
+ *   kron: Kronecker balancing (§3, footnote on balancing): 0 or 1 = none;
+ *        2, 4, 8 or 16 = pack this many consecutive coefficients of a and of
+ *        b into one coefficient with slots of w = bits_a + bits_b +
+ *        ceil(log2 min(na, nb)) + 1 bits (w <= 128), multiply the packed
+ *        polynomials with the other parameters, and decode the slots.  For
+ *        small coefficients at large degree, where the y transform dominates.
  */
 typedef struct {
-    int32_t K, M, r, y2, s, y1b;
+    int32_t K, M, r, y2, s, y1b, kron;
 } ipm_params;
 
 /* What a plan chose (ipm_choose / ipm_get_info). */
@@ -102,6 +108,11 @@ typedef struct {
     double log2_modulus;      /* log2(prod p) */
     double log2_bound;        /* log2(4H), H = min(na,nb)*K*2^(2M-2) */
     size_t workspace_bytes;   /* device bytes the plan allocates */
+    int32_t kron;             /* Kronecker packing factor (1 = none); when > 1,
+                                 K, M, r, Y... describe the packed product */
+    int32_t kron_w;           /* slot width in bits (0 when kron = 1) */
+    int64_t kron_na, kron_nb; /* packed coefficient counts */
+    uint32_t kron_bits_a, kron_bits_b;  /* packed bit bounds */
 } ipm_plan_info;
 
 /*
@@ -126,14 +137,19 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
 /*
  * Candidate plans of one shape for autotuning and cost-model dispatch: every
  * digit split K that meets the bounds, with the planner's tiles for it and
- * up to two tile variants (Y2 halved or doubled), each as the override set
+ * the tile variants Y2/2, 2 Y2 and S/2, each as the override set
  * that selects it, the plan it yields, and IPM_FEATURES numbers describing
- * it (log2 of na, nb, bits_a, bits_b, K, M, r, Y, Y2, S, Y1b, transform
- * points r*Y*2K, middle column length, total input bits; kernel variant
- * flags).  Writes at most `max` entries and returns how many exist
- * (negative status on an invalid shape).
+ * it (log2 of na, nb, bits_a, bits_b, K, Y, Y2, S, Y1b, transform points
+ * r*Y*2K, middle column length and total input bits; M/32, r, two kernel
+ * variant flags; log2 of the Kronecker packing factor; and log2 of the
+ * batch size capped at 16, which is 0 here: the learned dispatch sets it to
+ * log2(min(n, 16)) for a plan of n shapes).  Candidates with kron > 1 are
+ * listed when the slot width allows it (w <= 128), each factor with the
+ * planner's plan of the packed product and its K halved and doubled.
+ * Writes at most `max` entries and returns how many exist (negative status
+ * on an invalid shape).
  */
-#define IPM_FEATURES 16
+#define IPM_FEATURES 18
 typedef struct {
     ipm_params params;
     ipm_plan_info info;

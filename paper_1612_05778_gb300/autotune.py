@@ -1,5 +1,8 @@
 """Exhaustive autotuning sweep over candidate plans.
 
+The points are the balanced grid d = 2^6..2^20 x bits = 2^5..2^14 and 60
+seeded unbalanced shapes.
+
 For a product shape, every candidate plan (every valid digit split K with the
 planner's tiles and two tile variants, see ``ipm_candidates`` in ipm.h) is
 timed with CUDA events on seeded random operands generated on the device.
@@ -31,50 +34,73 @@ def _operands(torch, n: int, bits: int, gen):
     return limbs, neg
 
 
-def sweep_point(n: int, bits: int, seed: int, reps: int = 3, max_workspace: float = 120e9,
-                check=None) -> dict:
-    """Time every candidate plan of the balanced shape (n, n, bits, bits)."""
+BATCH = 16                  # batch size of the throughput timings
+BATCH_WORKSPACE = 4 << 30   # ... taken when B plans' workspace fits this
+
+
+def _time(fn, reps):
     import torch
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return min(times)
+
+
+def sweep_point(shape, seed: int, reps: int = 3, max_workspace: float = 120e9) -> dict:
+    """Time every candidate plan of shape (na, nb, bits_a, bits_b): alone
+    ("ms") and, where BATCH copies fit BATCH_WORKSPACE, per product in one
+    ipm_mul_batched call over BATCH products ("ms_batch")."""
+    import torch
+    na, nb, ba, bb = shape
     gen = torch.Generator(device="cuda")
-    gen.manual_seed(seed * 1_000_003 + n * 31 + bits)
-    a, an = _operands(torch, n, bits, gen)
-    b, bn = _operands(torch, n, bits, gen)
-    default = ipm.choose(n, n, bits, bits)
-    rec = {"n": n, "bits": bits, "seed": seed, "candidates": []}
+    gen.manual_seed(seed * 1_000_003 + na * 31 + nb * 7 + ba * 3 + bb)
+    a, an = _operands(torch, na, ba, gen)
+    b, bn = _operands(torch, nb, bb, gen)
+    default = ipm.choose(na, nb, ba, bb)
+    rec = {"shape": [na, nb, ba, bb], "n": na, "bits": ba, "seed": seed, "candidates": []}
     ref = None
-    for cand in ipm.candidates(n, n, bits, bits):
+    for cand in ipm.candidates(na, nb, ba, bb):
         info = cand["info"]
         entry = {"params": cand["params"], "features": cand["features"],
-                 "plan": {k: info[k] for k in ("K", "M", "r", "Y", "Y1", "Y2", "S", "Y1b")},
+                 "plan": {k: info[k] for k in ("K", "M", "r", "Y", "Y1", "Y2", "S", "Y1b", "kron", "kron_w")},
                  "workspace_bytes": info["workspace_bytes"]}
         if info["workspace_bytes"] > max_workspace:
             entry["ms"] = None
             entry["skipped"] = "workspace above %.0f GB" % (max_workspace / 1e9)
             rec["candidates"].append(entry)
             continue
-        plan = ipm.Plan((n, n, bits, bits), **cand["params"])
+        plan = ipm.Plan(tuple(shape), **cand["params"])
         c, cn = plan.empty_output()
         plan.mul(a, an, b, bn, c, cn)
         torch.cuda.synchronize()
         plan.sync()
-        times = []
-        for _ in range(reps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            plan.mul(a, an, b, bn, c, cn)
-            e1.record()
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-        entry["ms"] = min(times)
+        entry["ms"] = _time(lambda: plan.mul(a, an, b, bn, c, cn), reps)
         if ref is None:
             ref = (c, cn)
-            if check is not None:
-                check(a, an, b, bn, c, cn)
         elif not (torch.equal(ref[0], c) and torch.equal(ref[1], cn)):
-            raise AssertionError("candidate %s disagrees with %s at n=%d bits=%d"
-                                 % (cand["params"], rec["candidates"][0]["params"], n, bits))
-        entry["is_default"] = all(info[k] == default[k] for k in ("K", "M", "r", "Y2", "S", "Y1b"))
+            raise AssertionError("candidate %s disagrees with %s at %s"
+                                 % (cand["params"], rec["candidates"][0]["params"], shape))
+        entry["is_default"] = all(info[k] == default[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron"))
+        entry["ms_batch"] = None
+        if info["workspace_bytes"] * BATCH <= BATCH_WORKSPACE:
+            bplan = ipm.Plan([tuple(shape)] * BATCH, **cand["params"])
+            outs = [bplan.empty_output(i) for i in range(BATCH)]
+            ops = [(a, an, b, bn)] * BATCH
+            bplan.mul_batched(ops, outs)
+            torch.cuda.synchronize()
+            bplan.sync()
+            for co, cno in (outs[0], outs[-1]):
+                if not (torch.equal(ref[0], co) and torch.equal(ref[1], cno)):
+                    raise AssertionError("batched candidate %s disagrees at %s" % (cand["params"], shape))
+            entry["ms_batch"] = _time(lambda: bplan.mul_batched(ops, outs), reps) / BATCH
+            bplan.close()
+            del outs
         rec["candidates"].append(entry)
         plan.close()
         del c, cn
@@ -85,6 +111,10 @@ def sweep_point(n: int, bits: int, seed: int, reps: int = 3, max_workspace: floa
     rec["best_params"] = best["params"] if best else None
     rec["best_plan"] = best["plan"] if best else None
     rec["default_ms"] = dflt[0]["ms"] if dflt else None
+    tb = [c for c in timed if c.get("ms_batch") is not None]
+    rec["batch"] = BATCH
+    rec["best_ms_batch"] = min(c["ms_batch"] for c in tb) if tb else None
+    rec["default_ms_batch"] = dflt[0].get("ms_batch") if dflt else None
     del a, an, b, bn, ref
     torch.cuda.empty_cache()
     return rec
@@ -100,23 +130,10 @@ def main(argv=None) -> int:
     ap.add_argument("--max-points", type=int, default=0)
     ap.add_argument("--max-workspace", type=float, default=120e9,
                     help="skip candidates whose workspace exceeds this many bytes")
-    ap.add_argument("--check-bits", type=float, default=2**24,
-                    help="oracle check (mod 2^61-1 evaluation) when n*bits is at most this")
     args = ap.parse_args(argv)
-    import numpy as np
-    import oracle
 
-    Q = (1 << 61) - 1
-    rng = np.random.default_rng(args.seed)
-
-    def check(a, an, b, bn, c, cn):
-        t = int(rng.integers(2, Q - 1))
-        h = lambda x, s: (x.cpu().numpy().view(np.uint32), s.cpu().numpy())  # noqa: E731
-        A, B, C = h(a, an), h(b, bn), h(c, cn)
-        if oracle.eval_mod(C, t, Q) != oracle.eval_mod(A, t, Q) * oracle.eval_mod(B, t, Q) % Q:
-            raise AssertionError("product fails c(t) = a(t) b(t) mod 2^61-1")
-
-    grid = W.sweep_grid()
+    # the balanced grid, then seeded unbalanced shapes
+    grid = [(n, n, bits, bits) for n, bits in W.sweep_grid()] + W.sweep_unbalanced(args.seed)
     if args.max_points:
         grid = grid[: args.max_points]
     records = []
@@ -125,14 +142,13 @@ def main(argv=None) -> int:
     def fmt(ms):
         return "%.3f ms" % ms if ms is not None else "-"
 
-    for n, bits in grid:
-        rec = sweep_point(n, bits, args.seed, args.reps, args.max_workspace,
-                          check=check if n * bits <= args.check_bits else None)
-        rec["checked_mod_q"] = n * bits <= args.check_bits
+    for shape in grid:
+        rec = sweep_point(shape, args.seed, args.reps, args.max_workspace)
         records.append(rec)
-        print("n=%7d bits=%5d best %s %s default %s (%d candidates)" % (
-            n, bits, fmt(rec["best_ms"]), rec["best_plan"], fmt(rec["default_ms"]),
-            len(rec["candidates"])), file=sys.stderr, flush=True)
+        print("%s best %s %s default %s; batch of %d: best %s default %s (%d candidates)" % (
+            shape, fmt(rec["best_ms"]), rec["best_plan"], fmt(rec["default_ms"]), BATCH,
+            fmt(rec["best_ms_batch"]), fmt(rec["default_ms_batch"]), len(rec["candidates"])),
+            file=sys.stderr, flush=True)
         # rewritten after every point, so an interrupted sweep keeps its data
         with open(args.out + ".tmp", "w") as f:
             json.dump({"device": _device_name(), "seed": args.seed, "seconds": time.time() - t0,

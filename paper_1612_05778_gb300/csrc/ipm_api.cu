@@ -55,7 +55,8 @@ ipm_status run_one(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a, con
     if (!aligned16(a) || !aligned16(b) || !aligned16(c)) return IPM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const bool prof = plan->profiling;
-    if (!prof) return launch_product(sp, a, an, b, bn, c, cn, stream) ? IPM_ERR_CUDA : IPM_OK;
+    // (packed plans are timed as one phase: pack + product + unpack)
+    if (!prof || sp.kr.s > 1) return launch_product(sp, a, an, b, bn, c, cn, stream) ? IPM_ERR_CUDA : IPM_OK;
     // profiled: events around the three passes (a split plan's outer
     // passes count with the middle one)
     const KParams &kp = sp.kp;
@@ -112,7 +113,7 @@ VariantKey variant_of(const ShapePlan &sp) {
 std::vector<std::vector<int>> batch_groups(const std::vector<ShapePlan> &shapes) {
     std::map<VariantKey, std::vector<int>> by_variant;
     for (int i = 0; i < (int)shapes.size(); ++i)
-        if (shapes[(size_t)i].kp.Y1b == 1) by_variant[variant_of(shapes[(size_t)i])].push_back(i);
+        if (!runs_alone(shapes[(size_t)i])) by_variant[variant_of(shapes[(size_t)i])].push_back(i);
     std::vector<std::vector<int>> groups;
     for (auto &kv : by_variant) {
         auto &v = kv.second;
@@ -361,10 +362,11 @@ ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n, 
         if (ce != cudaSuccess) return cuda_status(ce);
         for (const auto &bl : plan->batch)
             if (launch_batch(bl, plan->d_ops, stream)) return IPM_ERR_CUDA;
-        // products whose middle transform is split run one after another
+        // products whose middle transform is split or whose operands are
+        // packed run one after another
         for (int32_t i = 0; i < n; ++i) {
             const ShapePlan &sp = plan->shapes[(size_t)i];
-            if (sp.kp.Y1b == 1) continue;
+            if (!runs_alone(sp)) continue;
             const ipm_operands &o = ops[i];
             if (launch_product(sp, o.a, o.a_neg, o.b, o.b_neg, o.c, o.c_neg, stream)) return IPM_ERR_CUDA;
         }

@@ -79,8 +79,26 @@ struct KParams {
 };
 
 // Host-side plan record for one shape.
+// Kronecker balancing: the product a*b is computed as the product of the
+// packed polynomials A'(z) = sum_k A'_k z^k, A'_k = sum_{u<s} a_{ks+u} 2^{uw}
+// (likewise B'), whose coefficient C'_k = sum_{t<2s-1} D_{k,t} 2^{tw} holds
+// the partial sums D_{k,t} = sum_{i+j=k, u+v=t} a_{is+u} b_{js+v} in
+// balanced w-bit slots; c_{ks+t} = D_{k,t} + D_{k-1,t+s}.  The packed
+// operands and product live after the transform workspace.
+constexpr int KRON_MAX = 16;
+constexpr int KRON_WMAX = 128;
+struct KronPlan {
+    int32_t s;                 // coefficients per packed coefficient (1 = none)
+    int32_t w;                 // slot width in bits
+    int64_t na, nb, nc;        // the original shape
+    int32_t la, lb, lc;
+    uint32_t bits_a, bits_b;
+    size_t off_a, off_an, off_b, off_bn, off_c, off_cn;  // word offsets from Z
+};
+
 struct ShapePlan {
     ipm_plan_info info;
+    KronPlan kr;          // s = 1: no packing (kp describes the product itself)
     KParams kp;           // pointers filled in by ipm_plan
     size_t smem_fwd, smem_mid, smem_inv, smem_outer;
     size_t z_words;       // workspace words
@@ -89,6 +107,10 @@ struct ShapePlan {
 
 // Planner (host only).  Fills sp (minus device pointers) or returns an error.
 ipm_status choose_plan(const ipm_shape &shape, const ipm_params *params, ShapePlan &sp);
+// Slot width of Kronecker packing for a shape (KronPlan).
+int kron_slot_width(const ipm_shape &shape);
+// Counts launches of this library's kernels (ipm_launch_count).
+void note_launches(int n);
 
 // Learned dispatch for n shapes (ipm_mlp.cu): params per shape and their
 // source (0 planner: params all zero, 1 tuning table, 2 model).
@@ -110,10 +132,19 @@ int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint
 int launch_middle(const KParams &kp, size_t smem, void *stream);
 int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, void *stream);
 int launch_outer(const KParams &kp, size_t smem, bool forward, void *stream);
-// The whole launch sequence of one product (forward, [outer], middle,
-// [outer inverse], inverse).  Returns 0 or -1 on a launch error.
+// The launch sequence of the transform product kp describes (forward,
+// [outer], middle, [outer inverse], inverse).  Returns 0 or -1.
+int launch_transform_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                             const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
+// Pack, transform product of the packed operands, unpack (ipm_kron.cu).
+int launch_kron_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                        const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
+// One whole product: launch_kron_product when sp.kr.s > 1, else
+// launch_transform_product.
 int launch_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                    const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
+// Products a batched call runs one at a time (split or packed plans).
+inline bool runs_alone(const ShapePlan &sp) { return sp.kp.Y1b > 1 || sp.kr.s > 1; }
 int set_kernel_attributes();
 
 // One group of a batched call: products that share the kernel variants,

@@ -29,6 +29,7 @@ namespace ipm {
 
 static std::atomic<int64_t> g_launches{0};
 int64_t launches_so_far() { return g_launches.load(); }
+void note_launches(int n) { g_launches.fetch_add(n); }
 
 // ---------------------------------------------------------------------------
 // Pass 1
@@ -804,6 +805,12 @@ int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, voi
 
 int launch_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                    const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream) {
+    if (sp.kr.s > 1) return launch_kron_product(sp, a, an, b, bn, c, cn, stream);
+    return launch_transform_product(sp, a, an, b, bn, c, cn, stream);
+}
+
+int launch_transform_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                             const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream) {
     const KParams &kp = sp.kp;
     if (launch_forward(kp, sp.smem_fwd, a, an, b, bn, stream)) return -1;
     if (kp.Y1b > 1 && launch_outer(kp, sp.smem_outer, true, stream)) return -1;

@@ -17,6 +17,7 @@
 // product.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -336,6 +337,8 @@ ipm_status dispatch_params(const ipm_shape *shapes, int32_t n, ipm_params *out, 
             const size_t at = cand.size();
             cand.resize(at + (size_t)m);
             ipm_candidates(&shapes[i], cand.data() + at, m);
+            const float batch = (float)std::log2((double)std::min<int32_t>(n, 16));
+            for (size_t j = at; j < cand.size(); ++j) cand[j].features[F - 1] = batch;
         }
         first[(size_t)n] = (int32_t)cand.size();
     }

@@ -257,7 +257,9 @@ TableLayout table_layout(int64_t Y, int64_t Y1, int32_t K) {
     return L;
 }
 
-ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp) {
+namespace {
+// The plan of the transform product itself (no packing).
+ipm_status choose_plan_direct(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp) {
     if (sh.deg_a < 0 || sh.deg_b < 0 || sh.bits_a < 1 || sh.bits_b < 1 ||
         sh.bits_a > 65536 || sh.bits_b > 65536)
         return IPM_ERR_ARG;
@@ -355,6 +357,88 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
     return IPM_OK;
 }
 
+size_t round4(size_t w) { return (w + 3) & ~(size_t)3; }
+
+}  // namespace
+
+// Kronecker slot width for a shape: bits_a + bits_b + ceil(log2 min(na, nb)) + 1.
+int kron_slot_width(const ipm_shape &sh) {
+    const int64_t mn = std::min(sh.deg_a, sh.deg_b) + 1;
+    return (int)(sh.bits_a + sh.bits_b) + ilog2((uint64_t)mn) + 1;
+}
+
+ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp) {
+    ipm_params P{};
+    if (prm) P = *prm;
+    if (P.kron < 0) return IPM_ERR_ARG;
+    if (sh.deg_a < 0 || sh.deg_b < 0 || sh.bits_a < 1 || sh.bits_b < 1 || sh.bits_a > 65536 ||
+        sh.bits_b > 65536)
+        return IPM_ERR_ARG;
+    const int64_t na = sh.deg_a + 1, nb = sh.deg_b + 1;
+    KronPlan kr{};
+    kr.s = 1;
+    kr.na = na;
+    kr.nb = nb;
+    kr.nc = na + nb - 1;
+    kr.la = (int)((sh.bits_a + 31) / 32);
+    kr.lb = (int)((sh.bits_b + 31) / 32);
+    kr.lc = (int)((sh.bits_a + sh.bits_b + (uint32_t)ilog2((uint64_t)std::min(na, nb)) + 31) / 32);
+    kr.bits_a = sh.bits_a;
+    kr.bits_b = sh.bits_b;
+    if (P.kron <= 1) {
+        P.kron = 0;
+        const ipm_status st = choose_plan_direct(sh, &P, sp);
+        if (st != IPM_OK) return st;
+        sp.kr = kr;
+        sp.info.kron = 1;
+        sp.info.kron_w = 0;
+        sp.info.kron_na = na;
+        sp.info.kron_nb = nb;
+        sp.info.kron_bits_a = sh.bits_a;
+        sp.info.kron_bits_b = sh.bits_b;
+        return IPM_OK;
+    }
+    if ((P.kron & (P.kron - 1)) || P.kron > KRON_MAX) return IPM_ERR_ARG;
+    const int w = kron_slot_width(sh);
+    if (w > KRON_WMAX) return IPM_ERR_ARG;
+    kr.s = P.kron;
+    kr.w = w;
+    const int64_t na2 = (na + kr.s - 1) / kr.s, nb2 = (nb + kr.s - 1) / kr.s;
+    // |A'_k| < 2^(bits_a + (s-1) w + 1): the slots hold disjoint bit ranges
+    const ipm_shape inner{na2 - 1, nb2 - 1, sh.bits_a + (uint32_t)((kr.s - 1) * w + 1),
+                          sh.bits_b + (uint32_t)((kr.s - 1) * w + 1)};
+    ipm_params Q = P;
+    Q.kron = 0;
+    const ipm_status st = choose_plan_direct(inner, &Q, sp);
+    if (st != IPM_OK) return st;
+    // packed operands and product after the transform workspace (16-byte aligned)
+    const KParams &kp = sp.kp;
+    size_t at = round4(sp.z_words);
+    kr.off_a = at;  at = round4(at + (size_t)kp.na * kp.la);
+    kr.off_an = at; at = round4(at + ((size_t)kp.na + 3) / 4);
+    kr.off_b = at;  at = round4(at + (size_t)kp.nb * kp.lb);
+    kr.off_bn = at; at = round4(at + ((size_t)kp.nb + 3) / 4);
+    kr.off_c = at;  at = round4(at + (size_t)kp.nc * kp.lc);
+    kr.off_cn = at; at = round4(at + ((size_t)kp.nc + 3) / 4);
+    ipm_plan_info &I = sp.info;
+    I.workspace_bytes += (at - sp.z_words) * 4;
+    sp.z_words = at;
+    sp.kr = kr;
+    I.kron = kr.s;
+    I.kron_w = w;
+    I.kron_na = na2;
+    I.kron_nb = nb2;
+    I.kron_bits_a = inner.bits_a;
+    I.kron_bits_b = inner.bits_b;
+    I.na = na;
+    I.nb = nb;
+    I.nc = kr.nc;
+    I.la = kr.la;
+    I.lb = kr.lb;
+    I.lc = kr.lc;
+    return IPM_OK;
+}
+
 void build_tables(ShapePlan &sp, uint2 *tab) {
     KParams &kp = sp.kp;
     const int64_t Y = kp.Y;
@@ -429,6 +513,8 @@ void build_tables(ShapePlan &sp, uint2 *tab) {
 
 namespace ipm {
 
+// Cost-model features of one candidate plan (the layout is given with
+// IPM_FEATURES in ipm.h).
 void candidate_features(const ipm_shape &sh, const ShapePlan &sp, float *f) {
     const ipm_plan_info &I = sp.info;
     auto lg = [](double x) { return (float)std::log2(std::max(1.0, x)); };
@@ -448,6 +534,8 @@ void candidate_features(const ipm_shape &sh, const ShapePlan &sp, float *f) {
     f[13] = lg((double)I.na * sh.bits_a + (double)I.nb * sh.bits_b);
     f[14] = sp.smem_fwd <= SMEM_FWD_3PERSM ? 1.0f : 0.0f;
     f[15] = sp.smem_inv <= SMEM_INV_2PERSM ? 1.0f : 0.0f;
+    f[16] = lg((double)sp.kr.s);
+    f[17] = 0.0f;  // log2(min(batch size, 16)): set by the dispatcher
 }
 
 }  // namespace ipm
@@ -463,7 +551,9 @@ extern "C" int32_t ipm_candidates(const ipm_shape *shape, ipm_candidate *out, in
         if (ipm::choose_plan(*shape, &prm, sp) != IPM_OK) return;
         for (auto &f : found) {
             const ipm_plan_info &a = f.second.info, &b = sp.info;
-            if (a.K == b.K && a.M == b.M && a.r == b.r && a.Y2 == b.Y2 && a.S == b.S && a.Y1b == b.Y1b) return;
+            if (a.K == b.K && a.M == b.M && a.r == b.r && a.Y2 == b.Y2 && a.S == b.S && a.Y1b == b.Y1b &&
+                a.kron == b.kron)
+                return;
         }
         found.emplace_back(prm, sp);
     };
@@ -478,6 +568,28 @@ extern "C" int32_t ipm_candidates(const ipm_shape *shape, ipm_candidate *out, in
             ipm_params v = prm;
             v.y2 = (int32_t)y2;
             add(v);
+        }
+        if (sp.info.S > 1) {  // a narrower middle slice
+            ipm_params v = prm;
+            v.s = sp.info.S / 2;
+            add(v);
+        }
+    }
+    // Kronecker balancing: each packing factor with the planner's plan of
+    // the packed product and its K halved and doubled
+    if (ipm::kron_slot_width(*shape) <= ipm::KRON_WMAX) {
+        for (int s = 2; s <= ipm::KRON_MAX; s *= 2) {
+            if (shape->deg_a + 1 < s && shape->deg_b + 1 < s) break;
+            ipm_params prm{};
+            prm.kron = s;
+            ipm::ShapePlan sp;
+            if (ipm::choose_plan(*shape, &prm, sp) != IPM_OK) continue;
+            add(prm);
+            for (int32_t k : {sp.info.K / 2, sp.info.K * 2}) {
+                ipm_params v = prm;
+                v.K = k;
+                if (k >= 2) add(v);
+            }
         }
     }
     const int32_t n = (int32_t)found.size();

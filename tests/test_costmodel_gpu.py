@@ -133,14 +133,16 @@ def test_tuning_table_takes_precedence(committed_model):
     assert ipm.dispatch(*shape) == ({}, "planner")
 
 
-def test_trained_model_beats_planner_on_held_out_points():
+@pytest.mark.parametrize("batch", [1, 16])
+def test_trained_model_beats_planner_on_held_out_points(batch):
     sweep = cm.load_sweep()
     train, held = cm.split_points(sweep["points"])
     model, loss = cm.train(train, epochs=4000, lr=1e-3, seed=0)
-    ev = cm.evaluate(model, held)
-    print("held-out regret: model %.4f (max %.3f, optimal %.0f%%), planner %.4f (max %.3f, optimal %.0f%%)" % (
-        ev["model"]["mean"], ev["model"]["max"], 100 * ev["model"]["optimal_fraction"],
-        ev["planner"]["mean"], ev["planner"]["max"], 100 * ev["planner"]["optimal_fraction"]))
-    assert ev["points"] == len(held) >= 40
+    ev = cm.evaluate(model, held, batch)
+    print("batch %d, held-out regret: model %.4f (max %.3f, optimal %.0f%%), planner %.4f (max %.3f, "
+          "optimal %.0f%%)" % (batch, ev["model"]["mean"], ev["model"]["max"],
+                               100 * ev["model"]["optimal_fraction"], ev["planner"]["mean"],
+                               ev["planner"]["max"], 100 * ev["planner"]["optimal_fraction"]))
+    assert ev["points"] >= 25
     assert ev["model"]["geomean_slowdown"] <= ev["planner"]["geomean_slowdown"]
     assert ev["model"]["mean"] <= ev["planner"]["mean"]

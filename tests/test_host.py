@@ -121,3 +121,33 @@ def test_unsupported_beyond_prime_order():
     with pytest.raises(ipm.IpmError) as e:
         ipm.choose(1 << 21, 1 << 21, 64, 64)
     assert e.value.status == 6
+
+
+# ---- Kronecker balancing plans (host only) ----------------------------------
+
+@pytest.mark.parametrize("shape,s", [((1000, 1000, 32, 32), 2), ((777, 1234, 20, 40), 8),
+                                     ((5, 3, 32, 32), 16), ((2048, 2048, 58, 58), 4)])
+def test_kron_plan_fields(shape, s):
+    na, nb, ba, bb = shape
+    info = ipm.choose(*shape, kron=s)
+    w = ba + bb + (min(na, nb) - 1).bit_length() + 1
+    assert info["kron"] == s and info["kron_w"] == w
+    assert info["kron_na"] == -(-na // s) and info["kron_nb"] == -(-nb // s)
+    assert info["kron_bits_a"] == ba + (s - 1) * w + 1
+    assert info["kron_bits_b"] == bb + (s - 1) * w + 1
+    # the output layout is the unpacked product's
+    plain = ipm.choose(*shape)
+    for k in ("na", "nb", "nc", "la", "lb", "lc"):
+        assert info[k] == plain[k]
+    assert plain["kron"] == 1 and plain["kron_w"] == 0
+    # the inner plan meets the CRT bound of the packed product
+    mn = min(info["kron_na"], info["kron_nb"])
+    assert info["log2_modulus"] > math.log2(mn) + math.log2(info["K"]) + 2 * info["M"]
+
+
+@pytest.mark.parametrize("shape,s", [((100, 100, 32, 32), 3), ((100, 100, 32, 32), 32),
+                                     ((100, 100, 70, 60), 2), ((100, 100, 32, 32), -1)])
+def test_kron_rejects_invalid(shape, s):
+    with pytest.raises(ipm.IpmError) as e:
+        ipm.choose(*shape, kron=s)
+    assert e.value.status == 1

@@ -174,3 +174,11 @@ def sweep_grid(dmin_log: int = 6, dmax_log: int = 20, bmin_log: int = 5, bmax_lo
     """The (degree, bits) grid of the dispatch sweep: powers of two on both axes."""
     return [(1 << dl, 1 << bl) for dl in range(dmin_log, dmax_log + 1)
             for bl in range(bmin_log, bmax_log + 1)]
+
+
+def sweep_unbalanced(seed: int = 4, count: int = 60):
+    """Unbalanced shapes added to the dispatch sweep: (na, nb, bits_a,
+    bits_b) drawn like the batched workload (log-uniform degrees in
+    [16, 65536], bit bounds in [16, 4096]), from the sweep's seed."""
+    shapes = batch_shapes(seed=seed, count=count, dmin=16, dmax=65536, bmin=16, bmax=4096)
+    return [(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes]
