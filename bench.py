@@ -15,8 +15,9 @@ host cores) on a bounded sample of the same workload per step and
 extrapolates to products/s.
 
 The timed plan is the one the learned dispatch picks (IPM_COSTMODEL with
-the committed GB300 cost model); `--plain` times the analytic planner's
-plan instead.  When the two differ, the plain plan is timed beside it on the
+the committed GB300 cost model and the sweep's table of measured bests,
+which takes precedence for shapes the sweep timed); `--plain` times the
+analytic planner's plan instead.  When the two differ, the plain plan is timed beside it on the
 same inputs and `speedup_vs_plain` is the ratio (1 when they coincide).
 
 --workload batch times one ipm_mul_batched call over 4096 products of
@@ -324,7 +325,7 @@ def run_batch(args):
     flags = 0
     if not args.plain:
         from paper_1612_05778_gb300 import costmodel as cmod
-        cmod.install()
+        cmod.install(points=cmod.load_sweep()["points"])  # model + the sweep's table
         flags = ipm.IPM_COSTMODEL
     plan = ipm.Plan(tuples, flags=flags)            # the chosen form
     plan_planner = ipm.Plan(tuples)                 # batched, analytic planner
@@ -370,7 +371,7 @@ def run_batch(args):
     ms_bp = timed(batched_planner, max(1, args.steps // 2))
     ms_p = timed(plain, max(1, args.steps // 2))
     plan_planner.sync()
-    changed = sum(any(a[k] != b[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron"))
+    changed = sum(any(a[k] != b[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron", "school"))
                   for a, b in zip(plan.infos, plan_planner.infos))
     clocks = sampler.stop()
     n = len(shapes)
@@ -414,14 +415,14 @@ def run_ours(args):
     dispatch = {"source": "planner (--plain)", "params": {}}
     if not args.plain:
         from paper_1612_05778_gb300 import costmodel as cmod
-        cmod.install()
+        cmod.install(points=cmod.load_sweep()["points"])  # model + the sweep's table
         flags = ipm.IPM_COSTMODEL
         prm, src = ipm.dispatch(*shape)
         dispatch = {"source": src, "params": prm}
     plan = ipm.Plan(shape, flags=flags)
     info = plan.info
     plain_plan = ipm.Plan(shape)
-    same_plan = all(plain_plan.info[k] == info[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron"))
+    same_plan = all(plain_plan.info[k] == info[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron", "school"))
     da, dan = ipm.to_device(*a)
     db, dbn = ipm.to_device(*b)
     c, cn = plan.empty_output()
@@ -560,7 +561,7 @@ def run_ours(args):
         "plain": ({"ms_per_step": plain_ms, "path": "analytic planner's plan"} if plain_ms else
                   {"path": "the analytic planner picks the same plan: one path, ratio 1"}),
         "config": {"workload": name, "na": sh.na, "nb": sh.nb, "bits": sh.bits_a, "lc": sh.lc,
-                   "plan": {k: info[k] for k in ("K", "M", "N", "r", "Y", "Y1", "Y2", "S", "Y1b", "kron")},
+                   "plan": {k: info[k] for k in ("K", "M", "N", "r", "Y", "Y1", "Y2", "S", "Y1b", "kron", "school")},
                    "dispatch": dispatch,
                    "primes": info["primes"], "parallelism": "replicas (one product per GPU)",
                    "l2": "flushed between timed steps (512 MiB write, outside the events)",

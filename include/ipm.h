@@ -91,9 +91,13 @@ typedef struct {
  *        ceil(log2 min(na, nb)) + 1 bits (w <= 128), multiply the packed
  *        polynomials with the other parameters, and decode the slots.  For
  *        small coefficients at large degree, where the y transform dominates.
+ *   school: 1 = the schoolbook family instead of the transform path:
+ *        c_k = sum a_i b_{k-i} by direct 32-bit limb products, one block per
+ *        output coefficient (small products only: La + Lb <= 256 and
+ *        na nb La Lb <= 2^27); the other fields must then be 0.
  */
 typedef struct {
-    int32_t K, M, r, y2, s, y1b, kron;
+    int32_t K, M, r, y2, s, y1b, kron, school;
 } ipm_params;
 
 /* What a plan chose (ipm_choose / ipm_get_info). */
@@ -113,6 +117,7 @@ typedef struct {
     int32_t kron_w;           /* slot width in bits (0 when kron = 1) */
     int64_t kron_na, kron_nb; /* packed coefficient counts */
     uint32_t kron_bits_a, kron_bits_b;  /* packed bit bounds */
+    int32_t school;           /* 1: schoolbook family (K, M, r, Y... are 0) */
 } ipm_plan_info;
 
 /*
@@ -136,20 +141,24 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
 
 /*
  * Candidate plans of one shape for autotuning and cost-model dispatch: every
- * digit split K that meets the bounds, with the planner's tiles for it and
- * the tile variants Y2/2, 2 Y2 and S/2, each as the override set
+ * digit split K from half to eight times the planner's that meets the
+ * bounds, with the planner's tiles for it and the tile variants Y2/2, 2 Y2,
+ * 4 Y2, S/2 and 2 S (where valid), each as the override set
  * that selects it, the plan it yields, and IPM_FEATURES numbers describing
  * it (log2 of na, nb, bits_a, bits_b, K, Y, Y2, S, Y1b, transform points
  * r*Y*2K, middle column length and total input bits; M/32, r, two kernel
- * variant flags; log2 of the Kronecker packing factor; and log2 of the
- * batch size capped at 16, which is 0 here: the learned dispatch sets it to
- * log2(min(n, 16)) for a plan of n shapes).  Candidates with kron > 1 are
- * listed when the slot width allows it (w <= 128), each factor with the
- * planner's plan of the packed product and its K halved and doubled.
+ * variant flags; log2 of the Kronecker packing factor; a schoolbook flag;
+ * and log2 of the batch size capped at 16, which is 0 here: the learned
+ * dispatch sets it to log2(min(n, 16)) for a plan of n shapes; for the
+ * schoolbook family the transform fields are 0 and the points feature is
+ * log2 of na nb La Lb).  Candidates with kron > 1 are listed when the slot
+ * width allows it (w <= 128), each factor with the planner's plan of the
+ * packed product and its K halved and doubled; the schoolbook candidate
+ * when its limits allow it.
  * Writes at most `max` entries and returns how many exist (negative status
  * on an invalid shape).
  */
-#define IPM_FEATURES 18
+#define IPM_FEATURES 19
 typedef struct {
     ipm_params params;
     ipm_plan_info info;

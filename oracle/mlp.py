@@ -18,7 +18,7 @@ from __future__ import annotations
 
 import numpy as np
 
-F = 18
+F = 19
 H = 32
 NPARAM = H * F + H + H * H + H + H + 1
 NFLOATS = 2 * F + 2 + NPARAM

@@ -37,7 +37,7 @@ class Shape(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("M", ctypes.c_int32), ("r", ctypes.c_int32),
                 ("y2", ctypes.c_int32), ("s", ctypes.c_int32), ("y1b", ctypes.c_int32),
-                ("kron", ctypes.c_int32)]
+                ("kron", ctypes.c_int32), ("school", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -50,7 +50,8 @@ class PlanInfo(ctypes.Structure):
                 ("log2_modulus", ctypes.c_double), ("log2_bound", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t), ("kron", ctypes.c_int32),
                 ("kron_w", ctypes.c_int32), ("kron_na", ctypes.c_int64), ("kron_nb", ctypes.c_int64),
-                ("kron_bits_a", ctypes.c_uint32), ("kron_bits_b", ctypes.c_uint32)]
+                ("kron_bits_a", ctypes.c_uint32), ("kron_bits_b", ctypes.c_uint32),
+                ("school", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "primes"}
@@ -58,7 +59,7 @@ class PlanInfo(ctypes.Structure):
         return d
 
 
-FEATURES = 18
+FEATURES = 19
 MLP_HIDDEN = 32
 MLP_PARAMS = MLP_HIDDEN * FEATURES + MLP_HIDDEN * MLP_HIDDEN + 3 * MLP_HIDDEN + 1
 MLP_FLOATS = 2 * FEATURES + 2 + MLP_PARAMS
@@ -124,10 +125,10 @@ def _check(st: int, what: str):
         raise IpmError(st, what)
 
 
-def _params(K=0, M=0, r=0, y2=0, s=0, y1b=0, kron=0):
-    if not (K or M or r or y2 or s or y1b or kron):
+def _params(K=0, M=0, r=0, y2=0, s=0, y1b=0, kron=0, school=0):
+    if not (K or M or r or y2 or s or y1b or kron or school):
         return None
-    return Params(K, M, r, y2, s, y1b, kron)
+    return Params(K, M, r, y2, s, y1b, kron, school)
 
 
 def choose(na: int, nb: int, bits_a: int, bits_b: int, **overrides) -> dict:

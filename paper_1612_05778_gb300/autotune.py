@@ -68,7 +68,7 @@ def sweep_point(shape, seed: int, reps: int = 3, max_workspace: float = 120e9) -
     for cand in ipm.candidates(na, nb, ba, bb):
         info = cand["info"]
         entry = {"params": cand["params"], "features": cand["features"],
-                 "plan": {k: info[k] for k in ("K", "M", "r", "Y", "Y1", "Y2", "S", "Y1b", "kron", "kron_w")},
+                 "plan": {k: info[k] for k in ("K", "M", "r", "Y", "Y1", "Y2", "S", "Y1b", "kron", "kron_w", "school")},
                  "workspace_bytes": info["workspace_bytes"]}
         if info["workspace_bytes"] > max_workspace:
             entry["ms"] = None
@@ -86,7 +86,7 @@ def sweep_point(shape, seed: int, reps: int = 3, max_workspace: float = 120e9) -
         elif not (torch.equal(ref[0], c) and torch.equal(ref[1], cn)):
             raise AssertionError("candidate %s disagrees with %s at %s"
                                  % (cand["params"], rec["candidates"][0]["params"], shape))
-        entry["is_default"] = all(info[k] == default[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron"))
+        entry["is_default"] = all(info[k] == default[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron", "school"))
         entry["ms_batch"] = None
         if info["workspace_bytes"] * BATCH <= BATCH_WORKSPACE:
             bplan = ipm.Plan([tuple(shape)] * BATCH, **cand["params"])

@@ -34,7 +34,8 @@ DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 SWEEP_GB300 = os.path.join(DATA, "sweep_gb300.json")
 MODEL_GB300 = os.path.join(DATA, "costmodel_gb300.json")
 
-_PLAN_KEYS = ("K", "M", "r", "Y2", "S", "Y1b", "kron")
+_PLAN_KEYS = ("K", "M", "r", "Y2", "S", "Y1b", "kron", "school")
+_PLAN_DEFAULTS = {"kron": 1, "school": 0}  # for records written before these keys existed
 
 
 def load_sweep(path: str = SWEEP_GB300) -> dict:
@@ -78,7 +79,7 @@ def current_features(point, batch: int = 1):
            for c in ipm.candidates(*shape_of(point))}
     out = []
     for c in _timed(point, batch):
-        key = tuple(c["plan"].get(k, 1) for k in _PLAN_KEYS)
+        key = tuple(c["plan"].get(k, _PLAN_DEFAULTS.get(k)) for k in _PLAN_KEYS)
         f = list(now.get(key, c["features"]))[:ipm.FEATURES]
         f += [0.0] * (ipm.FEATURES - len(f))
         f[ipm.FEATURES - 1] = batch_feature(batch)
@@ -107,7 +108,7 @@ def samples(points):
     return np.asarray(X, dtype=np.float32), np.asarray(y, dtype=np.float32)
 
 
-def train(points, epochs: int = 4000, lr: float = 1e-3, seed: int = 0):
+def train(points, epochs: int = 8000, lr: float = 1e-3, seed: int = 0):
     """Train on the given points' timings (GPU); returns (model, final mean loss)."""
     X, y = samples(points)
     return ipm.mlp_train(X, y, epochs=epochs, lr=lr, seed=seed)
@@ -184,7 +185,7 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--sweep", default=SWEEP_GB300)
     ap.add_argument("--out", default=None, help="write the trained model (JSON)")
-    ap.add_argument("--epochs", type=int, default=4000)
+    ap.add_argument("--epochs", type=int, default=8000)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args(argv)

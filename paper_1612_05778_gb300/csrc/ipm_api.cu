@@ -55,8 +55,9 @@ ipm_status run_one(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a, con
     if (!aligned16(a) || !aligned16(b) || !aligned16(c)) return IPM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const bool prof = plan->profiling;
-    // (packed plans are timed as one phase: pack + product + unpack)
-    if (!prof || sp.kr.s > 1) return launch_product(sp, a, an, b, bn, c, cn, stream) ? IPM_ERR_CUDA : IPM_OK;
+    // (packed and schoolbook plans are timed as one phase)
+    if (!prof || sp.kr.s > 1 || sp.school)
+        return launch_product(sp, a, an, b, bn, c, cn, stream) ? IPM_ERR_CUDA : IPM_OK;
     // profiled: events around the three passes (a split plan's outer
     // passes count with the middle one)
     const KParams &kp = sp.kp;
@@ -235,6 +236,7 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
     // primes are always the r largest of the table, so these fix every entry.
     std::map<std::tuple<int64_t, int64_t, int32_t, int32_t>, const uint2 *> cache;
     for (auto &sp : plan->shapes) {
+        if (sp.school) continue;  // no transform tables
         auto key = std::make_tuple(sp.kp.Y, sp.kp.Y1, sp.kp.K, sp.kp.r);
         std::vector<uint2> host((size_t)sp.kp.r * sp.table_words);
         build_tables(sp, host.data());  // also fills the scalar constants
@@ -269,6 +271,7 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
     // batched calls run a group's products at once: the workspace holds the
     // largest group (groups are cut at kBatchWorkspaceWords or one product)
     if (n > 1) zmax = std::max(zmax, batch_workspace_words(plan->shapes));
+    zmax = std::max<size_t>(zmax, 64);  // schoolbook-only plans need none
     void *d = nullptr;
     ce = cudaMalloc(&d, zmax * sizeof(uint32_t));
     if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }

@@ -99,6 +99,7 @@ struct KronPlan {
 struct ShapePlan {
     ipm_plan_info info;
     KronPlan kr;          // s = 1: no packing (kp describes the product itself)
+    bool school;          // schoolbook family: only kp's shape fields and err are used
     KParams kp;           // pointers filled in by ipm_plan
     size_t smem_fwd, smem_mid, smem_inv, smem_outer;
     size_t z_words;       // workspace words
@@ -143,8 +144,14 @@ int launch_kron_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *a
 // launch_transform_product.
 int launch_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                    const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
-// Products a batched call runs one at a time (split or packed plans).
-inline bool runs_alone(const ShapePlan &sp) { return sp.kp.Y1b > 1 || sp.kr.s > 1; }
+// The schoolbook family (ipm_school.cu): limits, shared memory, launch.
+constexpr int SCHOOL_MAX_COLUMNS = 256;                   // La + Lb
+constexpr double SCHOOL_MAX_LIMB_PRODUCTS = 134217728.0;  // na nb La Lb <= 2^27
+size_t school_smem(const KParams &kp);
+int launch_school(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b, const uint8_t *bn,
+                  uint32_t *c, uint8_t *cn, void *stream);
+// Products a batched call runs one at a time (split, packed or schoolbook).
+inline bool runs_alone(const ShapePlan &sp) { return sp.school || sp.kp.Y1b > 1 || sp.kr.s > 1; }
 int set_kernel_attributes();
 
 // One group of a batched call: products that share the kernel variants,

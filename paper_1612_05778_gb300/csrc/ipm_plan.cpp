@@ -181,14 +181,15 @@ size_t outer_smem(int64_t Y1b, int64_t W) { return (size_t)Y1b * (size_t)W * 4; 
 // for two CTAs per SM, a forward tile small enough for three, no split of
 // the middle transform (a split costs an extra pass over the data), and Y2
 // close to max(32, Y / 2048).  When Y1 is long, the middle transform may be
-// split as Y1 = Y1a * Y1b (Y1a <= 2048) with an outer pass over Y1b.
+// split as Y1 = Y1a * Y1b (Y1a <= 2048) with an outer pass over Y1b.  Slices
+// wider than 32 columns are used only when asked for (s).
 bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force, int64_t y1b_force,
                   Tiles &t) {
     const int64_t target = std::max<int64_t>(std::min<int64_t>(32, Y), Y / 2048);
     bool found = false;
     double best = 0;
     auto widest = [&](int64_t rows, bool tab, int force) {
-        for (int s = std::min(2 * K, 32); s >= 1; s >>= 1) {
+        for (int s = std::min(2 * K, force ? force : 32); s >= 1; s >>= 1) {
             if (force && s != force) continue;
             if (mid_smem(rows, s, tab) <= SMEM_MID_MAX) return s;
         }
@@ -385,10 +386,39 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
     kr.lc = (int)((sh.bits_a + sh.bits_b + (uint32_t)ilog2((uint64_t)std::min(na, nb)) + 31) / 32);
     kr.bits_a = sh.bits_a;
     kr.bits_b = sh.bits_b;
+    if (P.school < 0 || P.school > 1) return IPM_ERR_ARG;
+    if (P.school) {
+        if (P.K || P.M || P.r || P.y2 || P.s || P.y1b || P.kron > 1) return IPM_ERR_ARG;
+        if (kr.la + kr.lb > SCHOOL_MAX_COLUMNS) return IPM_ERR_ARG;
+        if ((double)na * (double)nb * kr.la * kr.lb > SCHOOL_MAX_LIMB_PRODUCTS) return IPM_ERR_ARG;
+        ShapePlan s{};
+        s.school = true;
+        s.kr = kr;
+        ipm_plan_info &I = s.info;
+        I.na = na; I.nb = nb; I.nc = kr.nc;
+        I.la = kr.la; I.lb = kr.lb; I.lc = kr.lc;
+        I.Y1b = 1;
+        I.kron = 1;
+        I.kron_na = na;
+        I.kron_nb = nb;
+        I.kron_bits_a = sh.bits_a;
+        I.kron_bits_b = sh.bits_b;
+        I.school = 1;
+        KParams &kp = s.kp;
+        std::memset(&kp, 0, sizeof(kp));
+        kp.na = na; kp.nb = nb; kp.nc = kr.nc;
+        kp.la = kr.la; kp.lb = kr.lb; kp.lc = kr.lc;
+        kp.bits_a = sh.bits_a; kp.bits_b = sh.bits_b;
+        kp.Y1b = 1;
+        sp = s;
+        return IPM_OK;
+    }
     if (P.kron <= 1) {
         P.kron = 0;
         const ipm_status st = choose_plan_direct(sh, &P, sp);
         if (st != IPM_OK) return st;
+        sp.school = false;
+        sp.info.school = 0;
         sp.kr = kr;
         sp.info.kron = 1;
         sp.info.kron_w = 0;
@@ -411,6 +441,8 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
     Q.kron = 0;
     const ipm_status st = choose_plan_direct(inner, &Q, sp);
     if (st != IPM_OK) return st;
+    sp.school = false;
+    sp.info.school = 0;
     // packed operands and product after the transform workspace (16-byte aligned)
     const KParams &kp = sp.kp;
     size_t at = round4(sp.z_words);
@@ -529,13 +561,14 @@ void candidate_features(const ipm_shape &sh, const ShapePlan &sp, float *f) {
     f[8] = lg((double)I.Y2);
     f[9] = lg((double)I.S);
     f[10] = lg((double)I.Y1b);
-    f[11] = lg((double)I.r * (double)I.Y * 2.0 * I.K);
+    f[11] = sp.school ? lg((double)I.na * (double)I.nb * I.la * I.lb) : lg((double)I.r * (double)I.Y * 2.0 * I.K);
     f[12] = lg((double)sp.kp.Y1a);
     f[13] = lg((double)I.na * sh.bits_a + (double)I.nb * sh.bits_b);
-    f[14] = sp.smem_fwd <= SMEM_FWD_3PERSM ? 1.0f : 0.0f;
-    f[15] = sp.smem_inv <= SMEM_INV_2PERSM ? 1.0f : 0.0f;
+    f[14] = !sp.school && sp.smem_fwd <= SMEM_FWD_3PERSM ? 1.0f : 0.0f;
+    f[15] = !sp.school && sp.smem_inv <= SMEM_INV_2PERSM ? 1.0f : 0.0f;
     f[16] = lg((double)sp.kr.s);
-    f[17] = 0.0f;  // log2(min(batch size, 16)): set by the dispatcher
+    f[17] = sp.school ? 1.0f : 0.0f;
+    f[18] = 0.0f;  // log2(min(batch size, 16)): set by the dispatcher
 }
 
 }  // namespace ipm
@@ -552,26 +585,30 @@ extern "C" int32_t ipm_candidates(const ipm_shape *shape, ipm_candidate *out, in
         for (auto &f : found) {
             const ipm_plan_info &a = f.second.info, &b = sp.info;
             if (a.K == b.K && a.M == b.M && a.r == b.r && a.Y2 == b.Y2 && a.S == b.S && a.Y1b == b.Y1b &&
-                a.kron == b.kron)
+                a.kron == b.kron && a.school == b.school)
                 return;
         }
         found.emplace_back(prm, sp);
     };
+    // digit splits from half to eight times the planner's K (the range in
+    // which the measured best plans lie), each with its tile variants
     for (int logK = 1; logK <= ipm::KMAX_LOG2; ++logK) {
+        if ((1 << logK) < base.info.K / 2 || (1 << logK) > base.info.K * 8) continue;
         ipm_params prm{};
         prm.K = 1 << logK;
         ipm::ShapePlan sp;
         if (ipm::choose_plan(*shape, &prm, sp) != IPM_OK) continue;
         add(prm);
-        for (int64_t y2 : {sp.info.Y2 / 2, sp.info.Y2 * 2}) {
+        for (int64_t y2 : {sp.info.Y2 / 2, sp.info.Y2 * 2, sp.info.Y2 * 4}) {
             if (y2 < 1) continue;
             ipm_params v = prm;
             v.y2 = (int32_t)y2;
             add(v);
         }
-        if (sp.info.S > 1) {  // a narrower middle slice
+        for (int32_t sl : {sp.info.S / 2, sp.info.S * 2}) {  // narrower and wider middle slices
+            if (sl < 1) continue;
             ipm_params v = prm;
-            v.s = sp.info.S / 2;
+            v.s = sl;
             add(v);
         }
     }
@@ -591,6 +628,11 @@ extern "C" int32_t ipm_candidates(const ipm_shape *shape, ipm_candidate *out, in
                 if (k >= 2) add(v);
             }
         }
+    }
+    {  // the schoolbook family, where its limits allow it
+        ipm_params prm{};
+        prm.school = 1;
+        add(prm);
     }
     const int32_t n = (int32_t)found.size();
     for (int32_t i = 0; i < n && i < max; ++i) {

@@ -97,15 +97,15 @@ def test_candidates_are_valid_distinct_and_include_the_planner(shape):
     for c in cands:
         info = ipm.choose(*shape, **c["params"])
         assert info == c["info"]
-        key = tuple(info[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron"))
+        key = tuple(info[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron", "school"))
         assert key not in keys
         keys.add(key)
         assert len(c["features"]) == ipm.FEATURES
         assert all(math.isfinite(v) for v in c["features"])
-        assert c["features"][4] == pytest.approx(math.log2(info["K"]))
+        assert c["features"][4] == pytest.approx(math.log2(max(info["K"], 1)))
         assert c["features"][6] == info["r"]
     d = ipm.choose(*shape)
-    assert tuple(d[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron")) in keys
+    assert tuple(d[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron", "school")) in keys
 
 
 def test_candidates_reject_bad_shape():

@@ -137,7 +137,7 @@ def test_tuning_table_takes_precedence(committed_model):
 def test_trained_model_beats_planner_on_held_out_points(batch):
     sweep = cm.load_sweep()
     train, held = cm.split_points(sweep["points"])
-    model, loss = cm.train(train, epochs=4000, lr=1e-3, seed=0)
+    model, loss = cm.train(train, epochs=8000, lr=1e-3, seed=0)
     ev = cm.evaluate(model, held, batch)
     print("batch %d, held-out regret: model %.4f (max %.3f, optimal %.0f%%), planner %.4f (max %.3f, "
           "optimal %.0f%%)" % (batch, ev["model"]["mean"], ev["model"]["max"],

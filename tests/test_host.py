@@ -151,3 +151,16 @@ def test_kron_rejects_invalid(shape, s):
     with pytest.raises(ipm.IpmError) as e:
         ipm.choose(*shape, kron=s)
     assert e.value.status == 1
+
+
+# ---- schoolbook plans (host only) ---------------------------------------------
+
+def test_school_plan_fields():
+    info = ipm.choose(300, 257, 255, 255, school=1)
+    plain = ipm.choose(300, 257, 255, 255)
+    assert info["school"] == 1 and plain["school"] == 0
+    for k in ("na", "nb", "nc", "la", "lb", "lc"):
+        assert info[k] == plain[k]
+    assert info["K"] == info["r"] == info["Y"] == 0
+    assert any(c["params"].get("school") for c in ipm.candidates(300, 257, 255, 255))
+    assert not any(c["params"].get("school") for c in ipm.candidates(1 << 15, 1 << 15, 4096, 4096))
