@@ -197,8 +197,10 @@ __device__ __forceinline__ const uint2 *pc_tables_i(const KParams &P, int t) { r
 
 // Pass 2 on one tile: columns [cs S, cs S + S) of the rows (pos, i1), prime t,
 // for i1 = Y1a pb + i1a, i1a < Y1a (without a split Y1a = Y1 and pb = 0).
-// SMTW: the omega_Y1 tables are copied to shared memory (else read from
-// global memory through the non-coherent cache).
+// SMTW: the omega_Y1 tables, and for every later stage a compact table of
+// its own sub-block length, are copied to shared memory (else every stage
+// reads the omega_Y1 tables in global memory through the non-coherent
+// cache).
 template <bool SMTW>
 __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int pb, int t) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -206,33 +208,67 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     const int pitch = S + 1;  // odd pitch for conflict-free strided gathers
     const int twoK = 2 * P.K;
     const int Y1 = (int)P.Y1a;  // this tile's column length
-    uint2 *twf_s = reinterpret_cast<uint2 *>(smem);     // omega_Y1^e, e < Y1 (no split)
-    uint2 *twi_s = twf_s + Y1;                          // omega_Y1^{-e}
-    const uint2 *twf = SMTW ? twf_s : pc_tables_f(P, t);
-    const uint2 *twi = SMTW ? twi_s : pc_tables_i(P, t);
-    uint32_t *A = reinterpret_cast<uint32_t *>(SMTW ? (void *)(twi_s + Y1) : (void *)smem);  // [Y1a][pitch]
-    uint32_t *B = A + (size_t)Y1 * pitch + 16;          // [Y1][pitch], shifted 16 banks
     const PrimeConst &pc = P.pc[t];
+    // SMTW: compact per-stage table pairs, back to back, then the tiles
+    uint2 *tab = reinterpret_cast<uint2 *>(smem);
+    int nst, sbase, sextra;
+    stage_split(P.logY1a, nst, sbase, sextra);
+    size_t tab_entries = 0;
+    {
+        int logLc = P.logY1a;
+        for (int i = 0; i < nst; ++i) {
+            tab_entries += (size_t)2 << logLc;
+            logLc -= sbase + (i < sextra ? 1 : 0);
+        }
+    }
+    uint32_t *A = reinterpret_cast<uint32_t *>(SMTW ? (void *)(tab + tab_entries) : (void *)smem);  // [Y1a][pitch]
+    uint32_t *B = A + (size_t)Y1 * pitch + 16;          // [Y1][pitch], shifted 16 banks
     const uint32_t p = pc.p, p2 = pc.p2;
     uint32_t *ZA = P.Z + (size_t)(t * 2 + 0) * (size_t)P.Y * twoK;
     const uint32_t *ZB = P.Z + (size_t)(t * 2 + 1) * (size_t)P.Y * twoK;
     const size_t base = ((size_t)pos * P.Y1 + (size_t)P.Y1a * pb) * twoK + (size_t)cs * S;
+    // Tile fill: thread -> (column c, first row r0), then rows r0 + k * rs.
+    // When S < 32 and the tile has whole 32-row blocks, the 32/S rows a warp
+    // touches are S apart (conflict-free at pitch S + 1, see rotate_rows):
+    // warp w, lane -> row 32 (w / S) + (w % S) + S (lane / S).  Rows grow by
+    // rs = blockDim / S per step (blockDim / 32 is a multiple of S).
+    const bool rot = S < 32 && S > 1 && Y1 >= 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = threadIdx.x & (S - 1);
+    const int r0 = rot ? ((warp >> logS) << 5) + (warp & (S - 1)) + ((lane >> logS) << logS)
+                       : (int)(threadIdx.x >> logS);
+    const int rs = blockDim.x >> logS;
+    const bool simple = S <= 32;  // else: one thread walks elements e = tid + k blockDim
     // A's slice, then B's, as two asynchronous copy groups: B is still in
     // flight while A is transformed
-    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
-        const int i1 = e >> logS, c = e & (S - 1);
-        cp_async4(A + i1 * pitch + c, ZA + base + (size_t)i1 * twoK + c);
+    if (simple) {
+        for (int i1 = r0; i1 < Y1; i1 += rs) cp_async4(A + i1 * pitch + c0, ZA + base + (size_t)i1 * twoK + c0);
+        cp_async_commit();
+        for (int i1 = r0; i1 < Y1; i1 += rs) cp_async4(B + i1 * pitch + c0, ZB + base + (size_t)i1 * twoK + c0);
+        cp_async_commit();
+    } else {
+        for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+            const int i1 = e >> logS, c = e & (S - 1);
+            cp_async4(A + i1 * pitch + c, ZA + base + (size_t)i1 * twoK + c);
+        }
+        cp_async_commit();
+        for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+            const int i1 = e >> logS, c = e & (S - 1);
+            cp_async4(B + i1 * pitch + c, ZB + base + (size_t)i1 * twoK + c);
+        }
+        cp_async_commit();
     }
-    cp_async_commit();
-    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
-        const int i1 = e >> logS, c = e & (S - 1);
-        cp_async4(B + i1 * pitch + c, ZB + base + (size_t)i1 * twoK + c);
-    }
-    cp_async_commit();
-    if (SMTW) {
-        for (int e = threadIdx.x; e < Y1; e += blockDim.x) {
-            twf_s[e] = __ldg(pc.t1_f + e);
-            twi_s[e] = __ldg(pc.t1_i + e);
+    if (SMTW) {  // stage i: omega_Lc^{+-e}, e < Lc = entries at stride Y1 / Lc (no split: Y1a = Y1)
+        uint2 *f = tab;
+        int logLc = P.logY1a;
+        for (int i = 0; i < nst; ++i) {
+            const int sh = P.logY1 - logLc;
+            for (int e = threadIdx.x; e < (1 << logLc); e += blockDim.x) {
+                f[e] = __ldg(pc.t1_f + ((size_t)e << sh));
+                f[e + (1 << logLc)] = __ldg(pc.t1_i + ((size_t)e << sh));
+            }
+            f += (size_t)2 << logLc;
+            logLc -= sbase + (i < sextra ? 1 : 0);
         }
     }
     cp_async_wait<1>();
@@ -241,15 +277,21 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     // copies finish while A is transformed), the pointwise product in
     // Montgomery form A*B*2^-32 (the 2^32 is put back by the scale factor of
     // the inverse pass) and the inverse step C, written over A
-    const TileMap am{A, S, S, 1, 0, pitch};
-    const TileMap bm{B, S, S, 1, 0, pitch};
-    ntt_convolve<SMTW>(am, bm, P.logY1a, twf, twi, P.logY1, p, p2, pc.mont, [] {
+    const int rl = S < 32 && S > 1 ? logS : 0;
+    const TileMap am{A, S, S, 1, 0, pitch, rl};
+    const TileMap bm{B, S, S, 1, 0, pitch, rl};
+    ntt_convolve<SMTW, SMTW>(am, bm, P.logY1a, SMTW ? tab : pc_tables_f(P, t), pc_tables_i(P, t), P.logY1, p,
+                             p2, pc.mont, [] {
         cp_async_wait<0>();
         __syncthreads();
     });
-    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
-        const int i1 = e >> logS, c = e & (S - 1);
-        ZA[base + (size_t)i1 * twoK + c] = red(A[i1 * pitch + c], p);
+    if (simple) {
+        for (int i1 = r0; i1 < Y1; i1 += rs) ZA[base + (size_t)i1 * twoK + c0] = red(A[i1 * pitch + c0], p);
+    } else {
+        for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+            const int i1 = e >> logS, c = e & (S - 1);
+            ZA[base + (size_t)i1 * twoK + c] = red(A[i1 * pitch + c], p);
+        }
     }
 }
 

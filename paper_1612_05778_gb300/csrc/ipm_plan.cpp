@@ -164,8 +164,11 @@ size_t inv_smem(int64_t Y2, int K, int r, int lc) {
     size_t tables = ((size_t)Y2 + (size_t)K) * 8;  // row twiddles, untwist
     return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources + tables;
 }
+// tiles of A and B, plus (tables) one omega table pair per stage: Y1
+// entries for the first, and fewer than Y1 / 7 for all later ones together
+// (the first stage has radix >= 8 when there are several)
 size_t mid_smem(int64_t Y1, int S, bool tables) {
-    return ((size_t)2 * Y1 * (S + 1) + 16) * 4 + (tables ? (size_t)2 * Y1 * 8 : 0);
+    return ((size_t)2 * Y1 * (S + 1) + 16) * 4 + (tables ? (size_t)2 * (Y1 + Y1 / 4 + 16) * 8 : 0);
 }
 // outer pass: Y1b rows x W consecutive words of one operand (W a power of
 // two >= 4, about OUTER_TILE_WORDS words per tile)

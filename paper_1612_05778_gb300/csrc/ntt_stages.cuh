@@ -126,7 +126,22 @@ struct TileMap {
     int tm;      // transforms per first-level group
     int ta, tb;  // strides of t % tm and t / tm
     int es;      // element stride
+    int rot;     // log2 T for tiles of T < 32 transforms at row pitch T + 1, else 0 (see rotate_rows)
 };
+
+// With T < 32 transforms at row pitch T + 1, a warp's gathers touch 32 / T
+// rows; rows T apart land on disjoint banks ((T + 1) T j = 0 mod T, and the
+// 32 / T offsets are distinct mod 32 for T = 2..16), consecutive rows do
+// not.  So in stages whose groups have at least 32 consecutive n1, the low
+// five bits of the group index are transposed (32 / T x T -> T x 32 / T)
+// before n1 is taken from them: a permutation of the groups, not of the
+// work.
+__device__ __forceinline__ int rotate_rows(int rest, int logT) {
+    const int logr = 5 - logT;
+    const int j = rest & ((1 << logr) - 1);
+    const int k = (rest >> logr) & ((1 << logT) - 1);
+    return (rest & ~31) | (j << logT) | k;
+}
 
 __device__ __forceinline__ int ilog2_if_pow2(int x) {
     return (x & (x - 1)) ? -1 : 31 - __clz(x);
@@ -164,9 +179,11 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
     const int tsh = logT - logLc;
     const int lT = ilog2_if_pow2(M.T), ltm = ilog2_if_pow2(M.tm);
     const int st = Lp * M.es;
+    const bool rot = M.rot && logLp >= 5;
     for (int g = threadIdx.x; g < total; g += blockDim.x) {
         int rest;
         uint32_t *tb = group_base(M, lT, ltm, g, rest);
+        if (rot) rest = rotate_rows(rest, M.rot);
         const int n1 = rest & (Lp - 1);
         const int blk = rest >> logLp;
         uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
@@ -214,9 +231,11 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
     const int tsh = logT - logLc;
     const int lT = ilog2_if_pow2(M.T), ltm = ilog2_if_pow2(M.tm);
     const int st = Lp * M.es;
+    const bool rot = M.rot && logLp >= 5;
     for (int g = threadIdx.x; g < total; g += blockDim.x) {
         int rest;
         uint32_t *tb = group_base(M, lT, ltm, g, rest);
+        if (rot) rest = rotate_rows(rest, M.rot);
         const int n1 = rest & (Lp - 1);
         const int blk = rest >> logLp;
         uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
@@ -326,7 +345,14 @@ __device__ __forceinline__ void stage_fused_pointwise(const TileMap &MA, const T
 // last stage each; A may be run before B's data are ready -- wait_b is
 // called in between), the fused last/pointwise/first-inverse stage, then
 // the remaining inverse stages on A.
-template <bool SM, typename WaitB>
+//
+// Twiddles.  COMPACT = false: every stage reads omega_T^{+-e} from twf /
+// twi (T = 2^logT, a multiple of 2^logL), stage i at stride T / Lc_i.
+// COMPACT = true: twf points at one table pair per stage, back to back --
+// stage i's omega_{Lc_i}^e then omega_{Lc_i}^{-e}, e < Lc_i -- so every
+// stage reads at stride 1 and the gathers of a warp stay on distinct
+// shared-memory banks (twi and logT are unused).
+template <bool SM, bool COMPACT, typename WaitB>
 __device__ __forceinline__ void ntt_convolve(const TileMap &MA, const TileMap &MB, int logL,
                                              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
                                              int logT, uint32_t p, uint32_t p2, uint32_t mont, WaitB wait_b) {
@@ -343,31 +369,57 @@ __device__ __forceinline__ void ntt_convolve(const TileMap &MA, const TileMap &M
         __syncthreads();
         return;
     }
-    int logLc = logL;
-    for (int i = 0; i + 1 < nst; ++i) {
-        const int b = base + (i < extra ? 1 : 0);
-        run_stage<true, SM>(b, MA, logL, logLc, twf, logT, p, p2);
-        logLc -= b;
+    // stage i's tables: (tf, ti, lg)
+    auto tables = [&](const uint2 *tab, int logLc, const uint2 *&tf, const uint2 *&ti, int &lg) {
+        if (COMPACT) {
+            tf = tab;
+            ti = tab + (1 << logLc);
+            lg = logLc;
+        } else {
+            tf = twf;
+            ti = twi;
+            lg = logT;
+        }
+    };
+    const uint2 *tf, *ti;
+    int lg;
+    for (int pass = 0; pass < 2; ++pass) {
+        const TileMap &M = pass ? MB : MA;
+        if (pass) wait_b();
+        const uint2 *tab = twf;
+        int logLc = logL;
+        for (int i = 0; i + 1 < nst; ++i) {
+            const int b = base + (i < extra ? 1 : 0);
+            tables(tab, logLc, tf, ti, lg);
+            run_stage<true, SM>(b, M, logL, logLc, tf, lg, p, p2);
+            tab += 2 << logLc;
+            logLc -= b;
+        }
     }
-    wait_b();
-    logLc = logL;
-    for (int i = 0; i + 1 < nst; ++i) {
-        const int b = base + (i < extra ? 1 : 0);
-        run_stage<true, SM>(b, MB, logL, logLc, twf, logT, p, p2);
-        logLc -= b;
+    // the last stage: its tables follow the earlier stages' tables
+    const uint2 *tab = twf;
+    {
+        int logLc = logL;
+        for (int i = 0; i + 1 < nst; ++i) {
+            tab += 2 << logLc;
+            logLc -= base + (i < extra ? 1 : 0);
+        }
     }
     const int blast = base + (nst - 1 < extra ? 1 : 0);
+    tables(tab, blast, tf, ti, lg);
     switch (blast) {
-        case 1: stage_fused_pointwise<2, SM>(MA, MB, logL, twf, twi, logT, p, p2, mont); break;
-        case 2: stage_fused_pointwise<4, SM>(MA, MB, logL, twf, twi, logT, p, p2, mont); break;
-        case 3: stage_fused_pointwise<8, SM>(MA, MB, logL, twf, twi, logT, p, p2, mont); break;
-        default: stage_fused_pointwise<16, SM>(MA, MB, logL, twf, twi, logT, p, p2, mont); break;
+        case 1: stage_fused_pointwise<2, SM>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
+        case 2: stage_fused_pointwise<4, SM>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
+        case 3: stage_fused_pointwise<8, SM>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
+        default: stage_fused_pointwise<16, SM>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
     }
-    logLc = blast;
+    int logLc = blast;
     for (int i = nst - 2; i >= 0; --i) {
         const int b = base + (i < extra ? 1 : 0);
         logLc += b;
-        run_stage<false, SM>(b, MA, logL, logLc, twi, logT, p, p2);
+        tab -= 2 << logLc;  // stage i's tables precede stage i+1's
+        tables(tab, logLc, tf, ti, lg);
+        run_stage<false, SM>(b, MA, logL, logLc, ti, lg, p, p2);
     }
 }
 
