@@ -240,6 +240,20 @@ ipm_status ipm_mul_host(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg
                         const uint32_t *b, const uint8_t *b_neg,
                         uint32_t *c, uint8_t *c_neg, ipm_stream_t stream);
 
+/*
+ * ipm_mul_host without the wait: the copies in, the product and the copies
+ * out are enqueued on `stream` and the call returns.  The result is in c
+ * and c_neg, and device errors are reported, after ipm_sync(plan, stream).
+ * The host buffers must stay valid until then and should be pinned (copies
+ * from pageable memory are not asynchronous).  Calls on one plan share its
+ * device buffers, so they must be ordered on one stream; a caller overlaps
+ * the copies of one product with the compute of another by using two plans
+ * on two streams.
+ */
+ipm_status ipm_mul_host_async(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg,
+                              const uint32_t *b, const uint8_t *b_neg,
+                              uint32_t *c, uint8_t *c_neg, ipm_stream_t stream);
+
 /* Device pointers of one product of a batch (layout as for ipm_mul). */
 typedef struct {
     const uint32_t *a;

@@ -93,6 +93,7 @@ def load_library(path: str | None = None):
     lib.ipm_get_info.argtypes = [V, I32, ctypes.POINTER(PlanInfo)]
     lib.ipm_mul.argtypes = [V, V, V, V, V, V, V, V]
     lib.ipm_mul_host.argtypes = [V, V, V, V, V, V, V, V]
+    lib.ipm_mul_host_async.argtypes = [V, V, V, V, V, V, V, V]
     lib.ipm_mul_batched.argtypes = [V, ctypes.POINTER(Operands), I32, V]
     lib.ipm_sync.argtypes = [V, V]
     lib.ipm_destroy.argtypes = [V]
@@ -112,6 +113,7 @@ def load_library(path: str | None = None):
     lib.ipm_strerror.restype = ctypes.c_char_p
     lib.ipm_launch_count.restype = ctypes.c_int64
     for name in ("ipm_choose", "ipm_plan", "ipm_plan_ex", "ipm_get_info", "ipm_mul", "ipm_mul_host",
+                 "ipm_mul_host_async",
                  "ipm_mul_batched", "ipm_sync", "ipm_destroy", "ipm_set_profiling", "ipm_phase_ms",
                  "ipm_mul_noalloc", "ipm_mlp_train", "ipm_mlp_grad", "ipm_mlp_predict",
                  "ipm_set_cost_model", "ipm_set_tuned", "ipm_dispatch"):
@@ -332,6 +334,21 @@ class Plan:
         _check(self._lib.ipm_mul_host(self._h, P(a), P(a_neg), P(b), P(b_neg), P(c), P(c_neg),
                                       _stream_handle(stream)), "ipm_mul_host")
         return c, c_neg
+
+    def mul_host_async(self, a: np.ndarray, a_neg: np.ndarray, b: np.ndarray, b_neg: np.ndarray,
+                       c: np.ndarray, c_neg: np.ndarray, stream=None):
+        """Enqueue c = a*b with host (numpy, preferably pinned) buffers on
+        `stream` and return at once; call sync(stream) before reading c.  The
+        buffers must stay alive until then."""
+        I = self.info
+        for x, shape, dt in ((a, (I["na"], I["la"]), np.uint32), (b, (I["nb"], I["lb"]), np.uint32),
+                             (a_neg, (I["na"],), np.uint8), (b_neg, (I["nb"],), np.uint8),
+                             (c, (I["nc"], I["lc"]), np.uint32), (c_neg, (I["nc"],), np.uint8)):
+            if x.shape != shape or x.dtype != dt or not x.flags.c_contiguous:
+                raise ValueError("host buffers must be contiguous %s arrays of shape %s" % (dt.__name__, shape))
+        P = lambda x: ctypes.c_void_p(x.ctypes.data)  # noqa: E731
+        _check(self._lib.ipm_mul_host_async(self._h, P(a), P(a_neg), P(b), P(b_neg), P(c), P(c_neg),
+                                            _stream_handle(stream)), "ipm_mul_host_async")
 
     def mul_batched(self, operands, outputs=None, stream=None):
         """operands: list of (a, a_neg, b, b_neg) device tensors matching the

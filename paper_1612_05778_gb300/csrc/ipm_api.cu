@@ -314,8 +314,8 @@ ipm_status ipm_mul(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg, con
     return IPM_OK;
 }
 
-ipm_status ipm_mul_host(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg, const uint32_t *b,
-                        const uint8_t *b_neg, uint32_t *c, uint8_t *c_neg, ipm_stream_t stream) {
+ipm_status ipm_mul_host_async(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg, const uint32_t *b,
+                              const uint8_t *b_neg, uint32_t *c, uint8_t *c_neg, ipm_stream_t stream) {
     if (!plan || plan->shapes.size() != 1) return IPM_ERR_ARG;
     if (!a || !a_neg || !b || !b_neg || !c || !c_neg) return IPM_ERR_ARG;
     const ipm_plan_info &I = plan->shapes[0].info;
@@ -343,6 +343,13 @@ ipm_status ipm_mul_host(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg
     if (st != IPM_OK) return st;
     if ((ce = cudaMemcpyAsync(c, io + oc, bc, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_status(ce);
     if ((ce = cudaMemcpyAsync(c_neg, io + ocn, (size_t)I.nc, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_status(ce);
+    return IPM_OK;
+}
+
+ipm_status ipm_mul_host(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg, const uint32_t *b,
+                        const uint8_t *b_neg, uint32_t *c, uint8_t *c_neg, ipm_stream_t stream) {
+    const ipm_status st = ipm_mul_host_async(plan, a, a_neg, b, b_neg, c, c_neg, stream);
+    if (st != IPM_OK) return st;
     return read_error(plan, stream);
 }
 

@@ -184,6 +184,32 @@ def test_bound_violation_is_reported():
     plan.sync()
 
 
+def test_mul_host_async_two_plans_two_streams():
+    """Products in flight on two plans and two streams, host buffers pinned;
+    every result equals the oracle's after the syncs."""
+    rng = np.random.default_rng(14)
+    shape = (600, 500, 300, 200)
+    ops = [(W.random_poly(rng, 600, 300), W.random_poly(rng, 500, 200)) for _ in range(4)]
+    plans = [ipm.Plan(shape) for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()  # noqa: E731
+    I = plans[0].info
+    outs = []
+    for i, (a, b) in enumerate(ops):
+        hc = torch.empty((I["nc"], I["lc"]), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        hcn = torch.empty((I["nc"],), dtype=torch.uint8).pin_memory().numpy()
+        ins = (pin(a[0]), pin(a[1]), pin(b[0]), pin(b[1]))
+        plans[i % 2].mul_host_async(*ins, hc, hcn, stream=streams[i % 2])
+        outs.append((ins, hc, hcn))
+        if i % 2 == 1:  # a plan's buffers are reused by its next call on the same stream
+            for pl, st in zip(plans, streams):
+                pl.sync(st)
+            for (_, hc2, hcn2), (a2, b2) in zip(outs[-2:], ops[i - 1:i + 1]):
+                assert_same((hc2, hcn2), oracle.polymul(a2, b2, I["lc"]))
+    for pl in plans:
+        pl.close()
+
+
 def test_mul_host_matches_oracle():
     rng = np.random.default_rng(4)
     a = W.random_poly(rng, 700, 500)
