@@ -235,16 +235,16 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def algorithmic_bytes(info):
-    """Algorithmic DRAM bytes of each pass for one product:
-    forward reads both operands and writes 2 r Y 2K residues; middle reads
-    them and writes r Y 2K; inverse reads r Y 2K and writes the output."""
+    """Algorithmic DRAM bytes of each pass for one product: forward reads
+    both operands and writes 2 r Y 2K residues; middle reads them and writes
+    r Y 2K; inverse reads r Y 2K and writes the output."""
     z = info["r"] * info["Y"] * 2 * info["K"] * 4
     inp = info["na"] * (info["la"] * 4 + 1) + info["nb"] * (info["lb"] * 4 + 1)
     out = info["nc"] * (info["lc"] * 4 + 1)
     return [inp + 2 * z, 3 * z, z + out]
 
 
-# 32-bit integer instructions per algorithmic unit (DESIGN.md): a lazy
+# 32-bit integer instructions per algorithmic unit: a lazy
 # Shoup butterfly (3 multiplies, 2 additions, 1 conditional subtraction and
 # the twiddle's subtraction) 7, a Shoup multiplication by a constant 3, a
 # Montgomery product 5.
