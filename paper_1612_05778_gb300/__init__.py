@@ -350,15 +350,13 @@ class Plan:
         _check(self._lib.ipm_mul_host_async(self._h, P(a), P(a_neg), P(b), P(b_neg), P(c), P(c_neg),
                                             _stream_handle(stream)), "ipm_mul_host_async")
 
-    def mul_batched(self, operands, outputs=None, stream=None):
-        """operands: list of (a, a_neg, b, b_neg) device tensors matching the
-        plan's shapes; returns the list of (c, c_neg)."""
+    def batch_args(self, operands, outputs):
+        """Validate a batch once and return its host array of device pointers
+        (ipm_operands[n]), reusable by mul_batched while the tensors live."""
         import torch
         n = len(self.shapes)
-        if len(operands) != n:
-            raise ValueError("need one operand set per plan shape")
-        if outputs is None:
-            outputs = [self.empty_output(i) for i in range(n)]
+        if len(operands) != n or len(outputs) != n:
+            raise ValueError("need one operand set and one output per plan shape")
         arr = (Operands * n)()
         for i, ((a, an, b, bn), (c, cn)) in enumerate(zip(operands, outputs)):
             I = self.infos[i]
@@ -368,6 +366,21 @@ class Plan:
                               _dptr(bn, torch.uint8, (I["nb"],)).value,
                               _dptr(c, torch.int32, (I["nc"], I["lc"])).value,
                               _dptr(cn, torch.uint8, (I["nc"],)).value)
+        return arr
+
+    def mul_batched(self, operands, outputs=None, stream=None):
+        """operands: list of (a, a_neg, b, b_neg) device tensors matching the
+        plan's shapes (returns the list of (c, c_neg)), or an array made by
+        batch_args (returns None)."""
+        n = len(self.shapes)
+        if isinstance(operands, ctypes.Array):
+            if len(operands) != n:
+                raise ValueError("need one operand set per plan shape")
+            _check(self._lib.ipm_mul_batched(self._h, operands, n, _stream_handle(stream)), "ipm_mul_batched")
+            return None
+        if outputs is None:
+            outputs = [self.empty_output(i) for i in range(n)]
+        arr = self.batch_args(operands, outputs)
         _check(self._lib.ipm_mul_batched(self._h, arr, n, _stream_handle(stream)), "ipm_mul_batched")
         return outputs
 

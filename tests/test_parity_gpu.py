@@ -184,6 +184,25 @@ def test_bound_violation_is_reported():
     plan.sync()
 
 
+def test_batched_with_prebuilt_arguments():
+    """mul_batched with the pointer array from batch_args, called twice."""
+    shapes = W.batch_shapes(seed=9, count=9, dmin=16, dmax=700, bmin=32, bmax=600)
+    ops = W.batch_operands(shapes, seed=9)
+    plan = ipm.Plan([(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes])
+    dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
+    outs = [plan.empty_output(i) for i in range(len(shapes))]
+    args = plan.batch_args(dev, outs)
+    for _ in range(2):
+        for c, cn in outs:
+            c.fill_(-1)
+            cn.fill_(7)
+        assert plan.mul_batched(args) is None
+        plan.sync()
+        for (a, b), (c, cn), info in zip(ops, outs, plan.infos):
+            assert_same(ipm.to_host(c, cn), oracle.polymul(a, b, info["lc"]))
+    plan.close()
+
+
 def test_mul_host_async_two_plans_two_streams():
     """Products in flight on two plans and two streams, host buffers pinned;
     every result equals the oracle's after the syncs."""
