@@ -22,8 +22,9 @@ same inputs and `speedup_vs_plain` is the ratio (1 when they coincide).
 
 --workload batch times one ipm_mul_batched call over 4096 products of
 log-uniform degrees in [16, 8192] and bit bounds in [32, 4096] (seed 3) with
-the learned dispatch and, beside it, the same batch with the analytic
-planner and the same products as 4096 ipm_mul calls (the plain path);
+the learned dispatch, its grouped launches replayed as one CUDA graph, and,
+beside it, the same batch with the analytic planner and the same products
+as 4096 ipm_mul calls (the plain path);
 `speedup_vs_plain` is the ratio to the plain path.
 
 Multi-GPU (torchrun): products are independent, so every rank multiplies its
@@ -327,7 +328,7 @@ def run_batch(args):
     if not args.plain:
         from paper_1612_05778_gb300 import costmodel as cmod
         cmod.install(points=cmod.load_sweep()["points"])  # model + the sweep's table
-        flags = ipm.IPM_COSTMODEL
+        flags = ipm.IPM_COSTMODEL | ipm.IPM_GRAPH
     plan = ipm.Plan(tuples, flags=flags)            # the chosen form
     plan_planner = ipm.Plan(tuples)                 # batched, analytic planner
     dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
@@ -397,7 +398,7 @@ def run_batch(args):
                       "path": "one ipm_mul C call per product (pointers prepared), analytic planner"},
             "batched_planner": {"ms_per_batch": ms_bp, "value": n / (ms_bp / 1e3),
                                 "path": "one ipm_mul_batched call, analytic planner"},
-            "dispatch": {"flags": "IPM_COSTMODEL" if flags else "none (--plain)",
+            "dispatch": {"flags": "IPM_COSTMODEL | IPM_GRAPH" if flags else "none (--plain)",
                          "products_with_another_plan": int(changed)},
             "config": {"workload": "batch: 4096 products, degrees log-uniform in [16, 8192], bits log-uniform "
                                    "in [32, 4096], random signs, unbalanced pairs, seed 3",

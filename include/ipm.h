@@ -69,6 +69,8 @@ typedef enum {
 #define IPM_SYNC 1u           /* calls synchronise and return device errors */
 #define IPM_COSTMODEL 2u      /* learned dispatch picks each shape's plan (see
                                  ipm_set_cost_model); ignored with params */
+#define IPM_GRAPH 4u          /* batched calls replay one CUDA graph of their
+                                 grouped launches (see ipm_mul_batched) */
 
 /* One product shape: a has deg_a+1 coefficients with |a_i| < 2^bits_a. */
 typedef struct {
@@ -270,7 +272,13 @@ typedef struct {
  * be reused as soon as the call returns.  The plan groups its shapes by
  * kernel variant (at most 4 GiB of workspace per group) and runs each
  * group's products together: three launches per group, every block finding
- * its product and tile in device tables built by ipm_plan.
+ * its product and tile in device tables built by ipm_plan.  Products whose
+ * plan splits the middle transform, packs coefficients or uses the
+ * schoolbook family are launched one by one after the groups.
+ * With IPM_GRAPH, the first call records the grouped launches into a CUDA
+ * graph (on a stream the plan owns; the kernels read all operand pointers
+ * from the plan's device table, which every call refreshes first) and every
+ * call launches that graph: one launch for all groups.
  */
 ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n,
                            ipm_stream_t stream);

@@ -25,6 +25,11 @@ struct ipm_plan_s {
     // batched calls (n > 1): groups of products launched together
     std::vector<BatchLaunch> batch;
     ipm_operands *d_ops = nullptr;    // operand pointers of the current call
+    // IPM_GRAPH: the grouped launches captured once into a CUDA graph
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_kernels = 0;
     // per-pass profiling events (ipm_set_profiling)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool profiling = false;
@@ -41,6 +46,9 @@ ipm_status cuda_status(cudaError_t e) {
 
 void free_plan(ipm_plan_s *p) {
     if (!p) return;
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     for (auto &e : p->ev)
         if (e) cudaEventDestroy(e);
     for (void *ptr : p->allocations) cudaFree(ptr);
@@ -146,6 +154,42 @@ size_t batch_workspace_words(const std::vector<ShapePlan> &shapes) {
         most = std::max(most, w);
     }
     return most;
+}
+
+// IPM_GRAPH: record the grouped launches of a batched call once, on a
+// plan-owned stream, into a CUDA graph.  Every kernel of the graph reads the
+// operand pointers from the plan's device table (d_ops), which each call
+// refreshes before launching the graph, so the graph stays valid for any
+// operands.  Products that run alone are launched outside the graph.
+ipm_status capture_batch(ipm_plan_s *plan) {
+    cudaError_t ce;
+    if (!plan->capture_stream) {
+        ce = cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) return cuda_status(ce);
+    }
+    const int64_t before = launches_so_far();
+    ce = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    bool failed = false;
+    for (const auto &bl : plan->batch)
+        if (launch_batch(bl, plan->d_ops, plan->capture_stream)) failed = true;
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(plan->capture_stream, &g);
+    const int captured = (int)(launches_so_far() - before);
+    note_launches(-captured);  // recorded, not run
+    if (failed || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return failed ? IPM_ERR_CUDA : cuda_status(ce);
+    }
+    ce = cudaGraphInstantiate(&plan->graph_exec, g, 0);
+    if (ce != cudaSuccess) {
+        cudaGraphDestroy(g);
+        plan->graph_exec = nullptr;
+        return cuda_status(ce);
+    }
+    plan->graph = g;
+    plan->graph_kernels = captured;
+    return IPM_OK;
 }
 
 ipm_status build_batch(ipm_plan_s *plan) {
@@ -370,8 +414,18 @@ ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n, 
         cudaError_t ce = cudaMemcpyAsync(plan->d_ops, ops, (size_t)n * sizeof(ipm_operands),
                                          cudaMemcpyHostToDevice, (cudaStream_t)stream);
         if (ce != cudaSuccess) return cuda_status(ce);
-        for (const auto &bl : plan->batch)
-            if (launch_batch(bl, plan->d_ops, stream)) return IPM_ERR_CUDA;
+        if (plan->flags & IPM_GRAPH) {
+            if (!plan->graph_exec) {
+                ipm_status st = capture_batch(plan);
+                if (st != IPM_OK) return st;
+            }
+            ce = cudaGraphLaunch(plan->graph_exec, (cudaStream_t)stream);
+            if (ce != cudaSuccess) return cuda_status(ce);
+            note_launches(plan->graph_kernels);
+        } else {
+            for (const auto &bl : plan->batch)
+                if (launch_batch(bl, plan->d_ops, stream)) return IPM_ERR_CUDA;
+        }
         // products whose middle transform is split or whose operands are
         // packed run one after another
         for (int32_t i = 0; i < n; ++i) {

@@ -203,6 +203,27 @@ def test_batched_with_prebuilt_arguments():
     plan.close()
 
 
+def test_batched_graph_replay():
+    """IPM_GRAPH: the grouped launches are recorded once and replayed; two
+    calls on different operand and output buffers (and a product that runs
+    outside the graph) all equal the oracle."""
+    shapes = W.batch_shapes(seed=12, count=10, dmin=16, dmax=900, bmin=32, bmax=700)
+    tuples = [(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes]
+    ipm.set_tuned([(tuples[3], {"school": 1})] if tuples[3][0] * tuples[3][1] < 1 << 18 else [])
+    try:
+        plan = ipm.Plan(tuples, flags=ipm.IPM_GRAPH | ipm.IPM_COSTMODEL)
+    finally:
+        ipm.set_tuned([])
+    for seed in (12, 13):
+        ops = W.batch_operands(shapes, seed=seed)
+        dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
+        outs = plan.mul_batched(dev)
+        plan.sync()
+        for (a, b), (c, cn), info in zip(ops, outs, plan.infos):
+            assert_same(ipm.to_host(c, cn), oracle.polymul(a, b, info["lc"]))
+    plan.close()
+
+
 def test_mul_host_async_two_plans_two_streams():
     """Products in flight on two plans and two streams, host buffers pinned;
     every result equals the oracle's after the syncs."""
