@@ -35,6 +35,19 @@ void note_launches(int n) { g_launches.fetch_add(n); }
 // Pass 1
 // ---------------------------------------------------------------------------
 
+// Pass 1's output: step-B twiddle of row pos, full reduction, store to row
+// (pos, i1) of the workspace.
+struct FwdStore {
+    uint32_t *Zt;
+    const uint2 *tw_rows;
+    size_t i1, Y1;
+    int twoK;
+    uint32_t p;
+    __device__ __forceinline__ void put(uint32_t *, int col, int pos, uint32_t v) const {
+        Zt[((size_t)pos * Y1 + i1) * twoK + col] = red(shoup(v, tw_rows[pos], p), p);
+    }
+};
+
 // Pass 1 on one tile: rows i = i1 + Y1*i2 (i2 < Y2) of operand op.
 __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
                                          const uint32_t *__restrict__ a, const uint8_t *__restrict__ an,
@@ -173,18 +186,12 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
             const TileMap xm{tile, 2 * nr, nr, pitch, K, 1};
             ntt_forward(xm, logK, pc.tx_f, logK + 1, p, p2);
         }
-        // 4. y step A: length-Y2 DFT down every column
+        // 4. y step A: length-Y2 DFT down every column; its last stage applies
+        //    the step-B twiddle omega_Y^{i1 k2} of row pos, reduces fully and
+        //    stores row (k2, i1) -- a warp's 32 consecutive columns per row
         const TileMap ym{tile, twoK, twoK, 1, 0, pitch};
-        ntt_forward(ym, P.logY2, pc.ty_f, P.logY, p, p2, upper_zero);
-        // 5. step B twiddle, full reduction, store rows (k2, i1)
-        uint32_t *Zt = P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK;
-        for (int e = threadIdx.x; e < Y2 * twoK; e += blockDim.x) {
-            const int pos = e >> (logK + 1), col = e & (twoK - 1);
-            const uint2 w = tw_rows[pos];
-            const uint32_t v = red(shoup(tile[(size_t)pos * pitch + col], w, p), p);
-            Zt[((size_t)pos * Y1 + i1) * twoK + col] = v;
-        }
-        __syncthreads();
+        const FwdStore out{P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK, tw_rows, (size_t)i1, (size_t)Y1, twoK, p};
+        ntt_forward_out(ym, P.logY2, pc.ty_f, P.logY, p, p2, upper_zero, out);
     }
 }
 
@@ -579,6 +586,15 @@ __device__ __forceinline__ void recombine_rows(const KParams &P, const uint32_t 
     }
 }
 
+// Pass 3's input: the step-B inverse twiddle of row pos, in [0, 2p).
+struct RowTwiddle {
+    const uint2 *tw_rows;
+    uint32_t p;
+    __device__ __forceinline__ uint32_t get(const uint32_t *a, int, int pos) const {
+        return shoup(*a, tw_rows[pos], p);
+    }
+};
+
 // Pass 3 on one tile: output rows i = i1 + Y1*i2 (i2 < Y2).
 __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t *__restrict__ c,
                                          uint8_t *__restrict__ cn) {
@@ -624,14 +640,10 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
             tw_rows[q] = __ldg(pc.ty_i + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
         for (int j = threadIdx.x; j < K; j += blockDim.x) tw_untw[j] = __ldg(pc.untw + j);
         __syncthreads();
-        for (int e = threadIdx.x; e < Y2 * twoK; e += blockDim.x) {
-            const int pos = e >> (logK + 1), col = e & (twoK - 1);
-            uint32_t *x = Rt + (size_t)pos * pitch + col;
-            *x = shoup(*x, tw_rows[pos], p);
-        }
-        __syncthreads();
+        // inverse y step A; its first stage applies the step-B twiddle
+        // omega_Y^{-i1 k2} of row pos as it loads
         const TileMap ym{Rt, twoK, twoK, 1, 0, pitch};
-        ntt_inverse(ym, P.logY2, pc.ty_i, P.logY, p, p2);
+        ntt_inverse_in(ym, P.logY2, pc.ty_i, P.logY, p, p2, RowTwiddle{tw_rows, p});
         if (nro > 0) {
             const TileMap xm{Rt, 2 * nro, nro, pitch, K, 1};
             ntt_inverse(xm, logK, pc.tx_i, logK + 1, p, p2);

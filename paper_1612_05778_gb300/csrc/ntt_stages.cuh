@@ -166,10 +166,17 @@ __device__ __forceinline__ uint32_t *group_base(const TileMap &m, int lT, int lt
 // One forward stage of radix R at sub-block length Lc = 2^logLc (L = 2^logL).
 // tw: table of omega_T^e (T = 2^logT), T a multiple of L.
 // HZ: the second half of every group's inputs is zero (not read).
-template <int R, bool SM, bool HZ = false>
+// Where a stage's outputs go: back to the tile (the default), or, for the
+// last stage of a transform, to any destination put(address in the tile,
+// transform t, element n, value) chooses.
+struct TileOut {
+    __device__ __forceinline__ void put(uint32_t *a, int, int, uint32_t v) const { *a = v; }
+};
+
+template <int R, bool SM, bool HZ = false, class Out = TileOut>
 __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
-                                          uint32_t p2) {
+                                          uint32_t p2, const Out &out = Out()) {
     constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
     Roots<R> rt;
     load_roots<R, SM>(rt, tw, logT);
@@ -212,16 +219,25 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
             else
                 dft_dif<R>(x, rt, p, p2);
         }
+        const int t = lT >= 0 ? (g & (M.T - 1)) : g % M.T;
+        const int n0 = (blk << logLc) + n1;
 #pragma unroll
-        for (int m = 0; m < R; ++m) base[m * st] = x[m];
+        for (int m = 0; m < R; ++m) out.put(base + m * st, t, n0 + m * Lp, x[m]);
     }
     __syncthreads();
 }
 
-template <int R, bool SM>
+// Where a stage's inputs come from: the tile (the default), or, for the
+// first stage of an inverse transform, any value get(address in the tile,
+// transform t, element n) makes of the tile's entry.
+struct TileIn {
+    __device__ __forceinline__ uint32_t get(const uint32_t *a, int, int) const { return *a; }
+};
+
+template <int R, bool SM, class In = TileIn>
 __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
-                                          uint32_t p2) {
+                                          uint32_t p2, const In &in = In()) {
     constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
     Roots<R> rt;
     load_roots<R, SM>(rt, tw, logT);
@@ -250,8 +266,10 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
 #pragma unroll
             for (int m = 1; m < R; ++m) x[m] = shoup(x[m], w[m], p);
         } else {  // first inverse stage: every twiddle is 1
+            const int t = lT >= 0 ? (g & (M.T - 1)) : g % M.T;
+            const int n0 = blk << logLc;
 #pragma unroll
-            for (int m = 0; m < R; ++m) x[m] = base[m * st];
+            for (int m = 0; m < R; ++m) x[m] = in.get(base + m * st, t, n0 + m);
         }
         dft_dit<R>(x, rt, p, p2);
 #pragma unroll
@@ -286,6 +304,53 @@ __device__ __forceinline__ void run_stage(int b, const TileMap &M, int logL, int
         case 3: FWD ? stage_dif<8, SM>(M, logL, logLc, tw, logT, p, p2) : stage_dit<8, SM>(M, logL, logLc, tw, logT, p, p2); break;
         default: FWD ? stage_dif<16, SM>(M, logL, logLc, tw, logT, p, p2) : stage_dit<16, SM>(M, logL, logLc, tw, logT, p, p2); break;
     }
+}
+
+// The last stage of a forward transform, radix 2^b, writing through out.
+template <bool SM, class Out>
+__device__ __forceinline__ void last_stage_out(int b, bool hz, const TileMap &M, int logL, int logLc,
+                                               const uint2 *__restrict__ tw, int logT, uint32_t p, uint32_t p2,
+                                               const Out &out) {
+    if (hz) {
+        switch (b) {
+            case 1: stage_dif<2, SM, true>(M, logL, logLc, tw, logT, p, p2, out); return;
+            case 2: stage_dif<4, SM, true>(M, logL, logLc, tw, logT, p, p2, out); return;
+            case 3: stage_dif<8, SM, true>(M, logL, logLc, tw, logT, p, p2, out); return;
+            default: stage_dif<16, SM, true>(M, logL, logLc, tw, logT, p, p2, out); return;
+        }
+    }
+    switch (b) {
+        case 1: stage_dif<2, SM, false>(M, logL, logLc, tw, logT, p, p2, out); return;
+        case 2: stage_dif<4, SM, false>(M, logL, logLc, tw, logT, p, p2, out); return;
+        case 3: stage_dif<8, SM, false>(M, logL, logLc, tw, logT, p, p2, out); return;
+        default: stage_dif<16, SM, false>(M, logL, logLc, tw, logT, p, p2, out); return;
+    }
+}
+
+// ntt_forward whose last stage hands every output to out.put instead of
+// writing it back to the tile (a length-1 transform hands over its input).
+template <bool SM = false, class Out>
+__device__ __forceinline__ void ntt_forward_out(const TileMap &M, int logL, const uint2 *__restrict__ tw,
+                                                int logT, uint32_t p, uint32_t p2, bool upper_zero,
+                                                const Out &out) {
+    int nst, base, extra;
+    stage_split(logL, nst, base, extra);
+    if (nst == 0) {
+        for (int t = threadIdx.x; t < M.T; t += blockDim.x) {
+            uint32_t *a = M.s + (t % M.tm) * M.ta + (t / M.tm) * M.tb;
+            out.put(a, t, 0, *a);
+        }
+        __syncthreads();
+        return;
+    }
+    int logLc = logL;
+    for (int i = 0; i + 1 < nst; ++i) {
+        const int b = base + (i < extra ? 1 : 0);
+        run_stage<true, SM>(b, M, logL, logLc, tw, logT, p, p2, upper_zero && i == 0);
+        logLc -= b;
+    }
+    last_stage_out<SM>(base + (nst - 1 < extra ? 1 : 0), upper_zero && nst == 1, M, logL, logLc, tw, logT, p, p2,
+                       out);
 }
 
 // Full forward transform of length 2^logL on every transform of the map
@@ -435,6 +500,38 @@ __device__ __forceinline__ void ntt_inverse(const TileMap &M, int logL, const ui
         const int b = base + (i < extra ? 1 : 0);
         logLc += b;
         run_stage<false, SM>(b, M, logL, logLc, tw, logT, p, p2);
+    }
+}
+
+// ntt_inverse whose first stage reads every input through in.get (a
+// length-1 transform writes in.get of its input back to the tile).
+template <bool SM = false, class In>
+__device__ __forceinline__ void ntt_inverse_in(const TileMap &M, int logL, const uint2 *__restrict__ tw,
+                                               int logT, uint32_t p, uint32_t p2, const In &in) {
+    int nst, base, extra;
+    stage_split(logL, nst, base, extra);
+    if (nst == 0) {
+        for (int t = threadIdx.x; t < M.T; t += blockDim.x) {
+            uint32_t *a = M.s + (t % M.tm) * M.ta + (t / M.tm) * M.tb;
+            *a = in.get(a, t, 0);
+        }
+        __syncthreads();
+        return;
+    }
+    int logLc = 0;
+    for (int i = nst - 1; i >= 0; --i) {
+        const int b = base + (i < extra ? 1 : 0);
+        logLc += b;
+        if (i == nst - 1) {  // the first inverse stage (every twiddle is 1)
+            switch (b) {
+                case 1: stage_dit<2, SM>(M, logL, logLc, tw, logT, p, p2, in); break;
+                case 2: stage_dit<4, SM>(M, logL, logLc, tw, logT, p, p2, in); break;
+                case 3: stage_dit<8, SM>(M, logL, logLc, tw, logT, p, p2, in); break;
+                default: stage_dit<16, SM>(M, logL, logLc, tw, logT, p, p2, in); break;
+            }
+        } else {
+            run_stage<false, SM>(b, M, logL, logLc, tw, logT, p, p2);
+        }
     }
 }
 
