@@ -202,6 +202,17 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
 __device__ __forceinline__ const uint2 *pc_tables_f(const KParams &P, int t) { return P.pc[t].t1_f; }
 __device__ __forceinline__ const uint2 *pc_tables_i(const KParams &P, int t) { return P.pc[t].t1_i; }
 
+// Pass 2's output: the product of column c, row i1 of a slice, fully
+// reduced, to the workspace.
+struct MidStore {
+    uint32_t *Zs;  // the slice's first word
+    int twoK;
+    uint32_t p;
+    __device__ __forceinline__ void put(uint32_t *, int c, int i1, uint32_t v) const {
+        Zs[(size_t)i1 * twoK + c] = red(v, p);
+    }
+};
+
 // Pass 2 on one tile: columns [cs S, cs S + S) of the rows (pos, i1), prime t,
 // for i1 = Y1a pb + i1a, i1a < Y1a (without a split Y1a = Y1 and pb = 0).
 // SMTW: the omega_Y1 tables, and for every later stage a compact table of
@@ -287,11 +298,15 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     const int rl = S < 32 && S > 1 ? logS : 0;
     const TileMap am{A, S, S, 1, 0, pitch, rl};
     const TileMap bm{B, S, S, 1, 0, pitch, rl};
-    ntt_convolve<SMTW, SMTW>(am, bm, P.logY1a, SMTW ? tab : pc_tables_f(P, t), pc_tables_i(P, t), P.logY1, p,
-                             p2, pc.mont, [] {
+    // the last inverse stage stores its outputs, fully reduced, to the
+    // workspace (rows i1, columns c of this slice)
+    const MidStore out{ZA + base, twoK, p};
+    const bool stored = ntt_convolve<SMTW, SMTW>(am, bm, P.logY1a, SMTW ? tab : pc_tables_f(P, t), pc_tables_i(P, t),
+                                                 P.logY1, p, p2, pc.mont, [] {
         cp_async_wait<0>();
         __syncthreads();
-    });
+    }, out);
+    if (stored) return;
     if (simple) {
         for (int i1 = r0; i1 < Y1; i1 += rs) ZA[base + (size_t)i1 * twoK + c0] = red(A[i1 * pitch + c0], p);
     } else {

@@ -234,10 +234,10 @@ struct TileIn {
     __device__ __forceinline__ uint32_t get(const uint32_t *a, int, int) const { return *a; }
 };
 
-template <int R, bool SM, class In = TileIn>
+template <int R, bool SM, class In = TileIn, class Out = TileOut>
 __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
-                                          uint32_t p2, const In &in = In()) {
+                                          uint32_t p2, const In &in = In(), const Out &out = Out()) {
     constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
     Roots<R> rt;
     load_roots<R, SM>(rt, tw, logT);
@@ -272,8 +272,10 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
             for (int m = 0; m < R; ++m) x[m] = in.get(base + m * st, t, n0 + m);
         }
         dft_dit<R>(x, rt, p, p2);
+        const int t = lT >= 0 ? (g & (M.T - 1)) : g % M.T;
+        const int n0 = (blk << logLc) + n1;
 #pragma unroll
-        for (int m = 0; m < R; ++m) base[m * st] = x[m];
+        for (int m = 0; m < R; ++m) out.put(base + m * st, t, n0 + m * Lp, x[m]);
     }
     __syncthreads();
 }
@@ -417,10 +419,15 @@ __device__ __forceinline__ void stage_fused_pointwise(const TileMap &MA, const T
 // stage i's omega_{Lc_i}^e then omega_{Lc_i}^{-e}, e < Lc_i -- so every
 // stage reads at stride 1 and the gathers of a warp stay on distinct
 // shared-memory banks (twi and logT are unused).
-template <bool SM, bool COMPACT, typename WaitB>
-__device__ __forceinline__ void ntt_convolve(const TileMap &MA, const TileMap &MB, int logL,
+//
+// The last inverse stage hands its outputs to out.put; the return value says
+// whether it did (false when the transform has fewer than two stages: the
+// results are then in MA's tile).
+template <bool SM, bool COMPACT, typename WaitB, class Out = TileOut>
+__device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &MB, int logL,
                                              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
-                                             int logT, uint32_t p, uint32_t p2, uint32_t mont, WaitB wait_b) {
+                                             int logT, uint32_t p, uint32_t p2, uint32_t mont, WaitB wait_b,
+                                             const Out &out = Out()) {
     int nst, base, extra;
     stage_split(logL, nst, base, extra);
     if (nst == 0) {  // length 1: the product of the single values
@@ -432,7 +439,7 @@ __device__ __forceinline__ void ntt_convolve(const TileMap &MA, const TileMap &M
             *a = montmul(*a, *b, p, mont);
         }
         __syncthreads();
-        return;
+        return false;
     }
     // stage i's tables: (tf, ti, lg)
     auto tables = [&](const uint2 *tab, int logLc, const uint2 *&tf, const uint2 *&ti, int &lg) {
@@ -484,8 +491,19 @@ __device__ __forceinline__ void ntt_convolve(const TileMap &MA, const TileMap &M
         logLc += b;
         tab -= 2 << logLc;  // stage i's tables precede stage i+1's
         tables(tab, logLc, tf, ti, lg);
-        run_stage<false, SM>(b, MA, logL, logLc, ti, lg, p, p2);
+        if (i > 0) {
+            run_stage<false, SM>(b, MA, logL, logLc, ti, lg, p, p2);
+        } else {  // the last inverse stage
+            const TileIn in;
+            switch (b) {
+                case 1: stage_dit<2, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
+                case 2: stage_dit<4, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
+                case 3: stage_dit<8, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
+                default: stage_dit<16, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
+            }
+        }
     }
+    return nst >= 2;
 }
 
 // Inverse of ntt_forward up to the factor 2^logL (tw: inverse table): the
