@@ -65,7 +65,9 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
     int64_t *dig = reinterpret_cast<int64_t *>(smem);            // [Y2][K]
     uint2 *tw_twist = reinterpret_cast<uint2 *>(dig + (size_t)Y2 * K);  // theta^j, j < K
     uint2 *tw_rows = tw_twist + K;                               // omega_Y^{i1 k2(pos)}, pos < Y2
-    uint8_t *signs = reinterpret_cast<uint8_t *>(tw_rows + Y2);  // sign of row i2
+    uint2 *tw_x = tw_rows + Y2;                                  // omega_K^e = theta^2e, e < K
+    uint2 *tw_y = tw_x + K;                                      // omega_Y2^e = omega_Y^(Y1 e), e < Y2
+    uint8_t *signs = reinterpret_cast<uint8_t *>(tw_y + Y2);     // sign of row i2
     uint32_t *tile = reinterpret_cast<uint32_t *>(signs + ((Y2 + 15) & ~15));  // [Y2][pitch]
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -156,9 +158,16 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         const PrimeConst &pc = P.pc[t];
         const uint32_t p = pc.p, p2 = pc.p2;
         const uint2 one = make_uint2(1u, pc.one_s), c32 = make_uint2(pc.c32, pc.c32_s);
-        for (int j = threadIdx.x; j < K; j += blockDim.x) tw_twist[j] = __ldg(pc.tx_f + j);
-        for (int q = threadIdx.x; q < Y2; q += blockDim.x)
+        // this prime's tables in shared memory: the transforms' twiddles are
+        // read by every warp as broadcasts, whatever their stride
+        for (int j = threadIdx.x; j < K; j += blockDim.x) {
+            tw_twist[j] = __ldg(pc.tx_f + j);
+            tw_x[j] = __ldg(pc.tx_f + 2 * j);
+        }
+        for (int q = threadIdx.x; q < Y2; q += blockDim.x) {
             tw_rows[q] = __ldg(pc.ty_f + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
+            tw_y[q] = __ldg(pc.ty_f + ((size_t)q << (P.logY - P.logY2)));
+        }
         __syncthreads();
         // 2. residues (cyclic half) and twisted residues theta^j a_ij (negacyclic half)
         for (int e = threadIdx.x; e < nr * K; e += blockDim.x) {
@@ -184,14 +193,14 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         // 3. x-DFTs of length K on both halves of the non-zero rows (omega_K = theta^2)
         if (nr > 0) {
             const TileMap xm{tile, 2 * nr, nr, pitch, K, 1};
-            ntt_forward(xm, logK, pc.tx_f, logK + 1, p, p2);
+            ntt_forward<true>(xm, logK, tw_x, logK, p, p2);
         }
         // 4. y step A: length-Y2 DFT down every column; its last stage applies
         //    the step-B twiddle omega_Y^{i1 k2} of row pos, reduces fully and
         //    stores row (k2, i1) -- a warp's 32 consecutive columns per row
         const TileMap ym{tile, twoK, twoK, 1, 0, pitch};
         const FwdStore out{P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK, tw_rows, (size_t)i1, (size_t)Y1, twoK, p};
-        ntt_forward_out(ym, P.logY2, pc.ty_f, P.logY, p, p2, upper_zero, out);
+        ntt_forward_out<true>(ym, P.logY2, tw_y, P.logY2, p, p2, upper_zero, out);
     }
 }
 
@@ -624,6 +633,8 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
     uint4 *sources = reinterpret_cast<uint4 *>(smem + (((size_t)r * plane * 4 + 15) & ~(size_t)15));  // [lc1]
     uint2 *tw_rows = reinterpret_cast<uint2 *>(sources + lc1);  // omega_Y^{-i1 k2(pos)}, pos < Y2
     uint2 *tw_untw = tw_rows + Y2;                               // scale theta^{-j}, j < K
+    uint2 *tw_x = tw_untw + K;                                   // omega_K^{-e}, e < K
+    uint2 *tw_y = tw_x + K;                                      // omega_Y2^{-e}, e < Y2
     for (int q = threadIdx.x; q < lc1; q += blockDim.x)
         sources[q] = M >= 32 ? limb_sources(q, M, r, twoK) : make_uint4(contrib_range(q, M, r, twoK), 0, 0, 0);
 
@@ -653,15 +664,19 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
         }
         for (int q = threadIdx.x; q < Y2; q += blockDim.x)
             tw_rows[q] = __ldg(pc.ty_i + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
-        for (int j = threadIdx.x; j < K; j += blockDim.x) tw_untw[j] = __ldg(pc.untw + j);
+        for (int q = threadIdx.x; q < Y2; q += blockDim.x) tw_y[q] = __ldg(pc.ty_i + ((size_t)q << (P.logY - P.logY2)));
+        for (int j = threadIdx.x; j < K; j += blockDim.x) {
+            tw_untw[j] = __ldg(pc.untw + j);
+            tw_x[j] = __ldg(pc.tx_i + 2 * j);
+        }
         __syncthreads();
         // inverse y step A; its first stage applies the step-B twiddle
         // omega_Y^{-i1 k2} of row pos as it loads
         const TileMap ym{Rt, twoK, twoK, 1, 0, pitch};
-        ntt_inverse_in(ym, P.logY2, pc.ty_i, P.logY, p, p2, RowTwiddle{tw_rows, p});
+        ntt_inverse_in<true>(ym, P.logY2, tw_y, P.logY2, p, p2, RowTwiddle{tw_rows, p});
         if (nro > 0) {
             const TileMap xm{Rt, 2 * nro, nro, pitch, K, 1};
-            ntt_inverse(xm, logK, pc.tx_i, logK + 1, p, p2);
+            ntt_inverse<true>(xm, logK, tw_x, logK, p, p2);
         }
         const uint2 sc = make_uint2(pc.scale, pc.scale_s);
         for (int e = threadIdx.x; e < nro * K; e += blockDim.x) {
