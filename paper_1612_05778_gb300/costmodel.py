@@ -163,11 +163,18 @@ def load_model(path: str = MODEL_GB300):
 
 
 def tuned_entries(points):
-    """Tuning-table entries (shape, params of the best measured candidate)."""
+    """Tuning-table entries (shape, params of the best measured candidate
+    that still plans with this library: the tile limits may have changed
+    since the sweep)."""
     out = []
     for p in points:
-        best = min(_timed(p), key=lambda c: c["ms"])
-        out.append((shape_of(p), best["params"]))
+        for c in sorted(_timed(p), key=lambda c: c["ms"]):
+            try:
+                ipm.choose(*shape_of(p), **c["params"])
+            except ipm.IpmError:
+                continue
+            out.append((shape_of(p), c["params"]))
+            break
     return out
 
 

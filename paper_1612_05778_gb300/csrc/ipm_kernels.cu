@@ -63,16 +63,31 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
     const int twoK = 2 * K;
     const int pitch = twoK + 1;  // odd row pitch: column walks hit distinct banks
     int64_t *dig = reinterpret_cast<int64_t *>(smem);            // [Y2][K]
-    uint2 *tw_twist = reinterpret_cast<uint2 *>(dig + (size_t)Y2 * K);  // theta^j, j < K
-    uint2 *tw_rows = tw_twist + K;                               // omega_Y^{i1 k2(pos)}, pos < Y2
-    uint2 *tw_x = tw_rows + Y2;                                  // omega_K^e = theta^2e, e < K
-    uint2 *tw_y = tw_x + K;                                      // omega_Y2^e = omega_Y^(Y1 e), e < Y2
-    uint8_t *signs = reinterpret_cast<uint8_t *>(tw_y + Y2);     // sign of row i2
+    // two sets of per-prime tables (prime t in set t & 1, the next prime's
+    // copied while this one is transformed): theta^j (j < K), omega_Y^{i1
+    // k2(pos)} (pos < Y2), omega_K^e = theta^2e (e < K), omega_Y2^e (e < Y2)
+    uint2 *tw_sets = reinterpret_cast<uint2 *>(dig + (size_t)Y2 * K);
+    const int set_len = 2 * (K + Y2);
+    uint8_t *signs = reinterpret_cast<uint8_t *>(tw_sets + 2 * set_len);  // sign of row i2
     uint32_t *tile = reinterpret_cast<uint32_t *>(signs + ((Y2 + 15) & ~15));  // [Y2][pitch]
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint64_t mmask = (1ull << M) - 1;
     const uint64_t halfM = 1ull << (M - 1);
+    auto prefetch_tables = [&](int t) {
+        const PrimeConst &pq = P.pc[t];
+        uint2 *set = tw_sets + (t & 1) * set_len;
+        for (int j = threadIdx.x; j < K; j += blockDim.x) {
+            cp_async8(set + j, pq.tx_f + j);
+            cp_async8(set + K + Y2 + j, pq.tx_f + 2 * j);
+        }
+        for (int q = threadIdx.x; q < Y2; q += blockDim.x) {
+            cp_async8(set + K + q, pq.ty_f + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
+            cp_async8(set + 2 * K + Y2 + q, pq.ty_f + ((size_t)q << (P.logY - P.logY2)));
+        }
+        cp_async_commit();
+    };
+    prefetch_tables(0);  // in flight during the digit split
 
     // 1. Balanced base-2^M digits of every row (one warp per row).  Digits
     //    j < K-1 follow the carry rule t = u_j + carry, digit = t - 2^M and
@@ -158,17 +173,20 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         const PrimeConst &pc = P.pc[t];
         const uint32_t p = pc.p, p2 = pc.p2;
         const uint2 one = make_uint2(1u, pc.one_s), c32 = make_uint2(pc.c32, pc.c32_s);
-        // this prime's tables in shared memory: the transforms' twiddles are
-        // read by every warp as broadcasts, whatever their stride
-        for (int j = threadIdx.x; j < K; j += blockDim.x) {
-            tw_twist[j] = __ldg(pc.tx_f + j);
-            tw_x[j] = __ldg(pc.tx_f + 2 * j);
-        }
-        for (int q = threadIdx.x; q < Y2; q += blockDim.x) {
-            tw_rows[q] = __ldg(pc.ty_f + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
-            tw_y[q] = __ldg(pc.ty_f + ((size_t)q << (P.logY - P.logY2)));
+        // this prime's tables in shared memory (the transforms' twiddles are
+        // read by every warp as broadcasts, whatever their stride); the next
+        // prime's are copied meanwhile
+        if (t + 1 < P.r) {
+            prefetch_tables(t + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const uint2 *tw_twist = tw_sets + (t & 1) * set_len;
+        const uint2 *tw_rows = tw_twist + K;
+        const uint2 *tw_x = tw_rows + Y2;
+        const uint2 *tw_y = tw_x + K;
         // 2. residues (cyclic half) and twisted residues theta^j a_ij (negacyclic half)
         for (int e = threadIdx.x; e < nr * K; e += blockDim.x) {
             const int i2 = e >> logK, j = e & (K - 1);
@@ -266,6 +284,20 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
                        : (int)(threadIdx.x >> logS);
     const int rs = blockDim.x >> logS;
     const bool simple = S <= 32;  // else: one thread walks elements e = tid + k blockDim
+    if (SMTW) {  // stage i: omega_Lc^{+-e}, e < Lc = entries at stride Y1 / Lc (no split: Y1a = Y1),
+                 // copied asynchronously with A's slice
+        uint2 *f = tab;
+        int logLc = P.logY1a;
+        for (int i = 0; i < nst; ++i) {
+            const int sh = P.logY1 - logLc;
+            for (int e = threadIdx.x; e < (1 << logLc); e += blockDim.x) {
+                cp_async8(f + e, pc.t1_f + ((size_t)e << sh));
+                cp_async8(f + e + (1 << logLc), pc.t1_i + ((size_t)e << sh));
+            }
+            f += (size_t)2 << logLc;
+            logLc -= sbase + (i < sextra ? 1 : 0);
+        }
+    }
     // A's slice, then B's, as two asynchronous copy groups: B is still in
     // flight while A is transformed
     if (simple) {
@@ -284,19 +316,6 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
             cp_async4(B + i1 * pitch + c, ZB + base + (size_t)i1 * twoK + c);
         }
         cp_async_commit();
-    }
-    if (SMTW) {  // stage i: omega_Lc^{+-e}, e < Lc = entries at stride Y1 / Lc (no split: Y1a = Y1)
-        uint2 *f = tab;
-        int logLc = P.logY1a;
-        for (int i = 0; i < nst; ++i) {
-            const int sh = P.logY1 - logLc;
-            for (int e = threadIdx.x; e < (1 << logLc); e += blockDim.x) {
-                f[e] = __ldg(pc.t1_f + ((size_t)e << sh));
-                f[e + (1 << logLc)] = __ldg(pc.t1_i + ((size_t)e << sh));
-            }
-            f += (size_t)2 << logLc;
-            logLc -= sbase + (i < sextra ? 1 : 0);
-        }
     }
     cp_async_wait<1>();
     __syncthreads();
@@ -631,10 +650,10 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
     uint32_t *R = reinterpret_cast<uint32_t *>(smem);  // [r][Y2][pitch]
     const int lc1 = P.lc + 1;
     uint4 *sources = reinterpret_cast<uint4 *>(smem + (((size_t)r * plane * 4 + 15) & ~(size_t)15));  // [lc1]
-    uint2 *tw_rows = reinterpret_cast<uint2 *>(sources + lc1);  // omega_Y^{-i1 k2(pos)}, pos < Y2
-    uint2 *tw_untw = tw_rows + Y2;                               // scale theta^{-j}, j < K
-    uint2 *tw_x = tw_untw + K;                                   // omega_K^{-e}, e < K
-    uint2 *tw_y = tw_x + K;                                      // omega_Y2^{-e}, e < Y2
+    // per-prime tables, copied with the prime's rows: omega_Y^{-i1 k2(pos)}
+    // (pos < Y2), omega_K^{-e} (e < K), omega_Y2^{-e} (e < Y2)
+    uint2 *tw_sets = reinterpret_cast<uint2 *>(sources + lc1);
+    const int set_len = 2 * Y2 + K;
     for (int q = threadIdx.x; q < lc1; q += blockDim.x)
         sources[q] = M >= 32 ? limb_sources(q, M, r, twoK) : make_uint4(contrib_range(q, M, r, twoK), 0, 0, 0);
 
@@ -647,6 +666,13 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
             const int pos = e >> (logK + 1), col = e & (twoK - 1);
             cp_async4(R + (size_t)t * plane + (size_t)pos * pitch + col, Zt + ((size_t)pos * Y1 + i1) * twoK + col);
         }
+        const PrimeConst &pq = P.pc[t];
+        uint2 *set = tw_sets + t * set_len;
+        for (int q = threadIdx.x; q < Y2; q += blockDim.x) {
+            cp_async8(set + q, pq.ty_i + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
+            cp_async8(set + Y2 + K + q, pq.ty_i + ((size_t)q << (P.logY - P.logY2)));
+        }
+        for (int j = threadIdx.x; j < K; j += blockDim.x) cp_async8(set + Y2 + j, pq.tx_i + 2 * j);
         cp_async_commit();
     }
     for (int t = 0; t < r; ++t) {
@@ -662,14 +688,11 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
             case 4: cp_async_wait<4>(); break;
             default: cp_async_wait<5>(); break;
         }
-        for (int q = threadIdx.x; q < Y2; q += blockDim.x)
-            tw_rows[q] = __ldg(pc.ty_i + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
-        for (int q = threadIdx.x; q < Y2; q += blockDim.x) tw_y[q] = __ldg(pc.ty_i + ((size_t)q << (P.logY - P.logY2)));
-        for (int j = threadIdx.x; j < K; j += blockDim.x) {
-            tw_untw[j] = __ldg(pc.untw + j);
-            tw_x[j] = __ldg(pc.tx_i + 2 * j);
-        }
         __syncthreads();
+        const uint2 *tw_rows = tw_sets + t * set_len;
+        const uint2 *tw_x = tw_rows + Y2;
+        const uint2 *tw_y = tw_x + K;
+        const uint2 *tw_untw = pc.untw;  // read once per element, contiguously
         // inverse y step A; its first stage applies the step-B twiddle
         // omega_Y^{-i1 k2} of row pos as it loads
         const TileMap ym{Rt, twoK, twoK, 1, 0, pitch};

@@ -155,13 +155,13 @@ struct Tiles {
 };
 
 size_t fwd_smem(int64_t Y2, int K) {
-    // digits, twist / row / x / y twiddles, signs, tile
-    return (size_t)Y2 * K * 8 + 2 * ((size_t)K + (size_t)Y2) * 8 + (((size_t)Y2 + 15) & ~(size_t)15) +
+    // digits, two sets of twist / row / x / y twiddles, signs, tile
+    return (size_t)Y2 * K * 8 + 4 * ((size_t)K + (size_t)Y2) * 8 + (((size_t)Y2 + 15) & ~(size_t)15) +
            (size_t)Y2 * (2 * K + 1) * 4;
 }
 size_t inv_smem(int64_t Y2, int K, int r, int lc) {
     size_t sources = ((size_t)lc + 1) * 16;  // one uint4 per limb
-    size_t tables = 2 * ((size_t)Y2 + (size_t)K) * 8;  // row / untwist / x / y twiddles
+    size_t tables = (size_t)r * (2 * (size_t)Y2 + (size_t)K) * 8;  // per prime: row / x / y twiddles
     return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources + tables;
 }
 // tiles of A and B, plus (tables) one omega table pair per stage: Y1

@@ -58,6 +58,11 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) 
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
+// 8-byte asynchronous copy (both addresses 8-byte aligned).
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
 // 16-byte copy through L2 only (both addresses 16-byte aligned).
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
