@@ -87,7 +87,6 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         }
         cp_async_commit();
     };
-    prefetch_tables(0);  // in flight during the digit split
 
     // 1. Balanced base-2^M digits of every row (one warp per row).  Digits
     //    j < K-1 follow the carry rule t = u_j + carry, digit = t - 2^M and
@@ -104,9 +103,12 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
     //    row i2 fits at tile + i2 * pitch), all loads in flight at once
     for (int e = threadIdx.x; e < nr * L; e += blockDim.x) {
         const int i2 = e / L, l = e - i2 * L;
-        tile[(size_t)i2 * pitch + l] = __ldg(X + (size_t)(i1 + Y1 * i2) * L + l);
+        cp_async4(tile + (size_t)i2 * pitch + l, X + (size_t)(i1 + Y1 * i2) * L + l);
     }
+    cp_async_commit();
+    prefetch_tables(0);  // the first prime's tables fly during the digit split
     for (int i2 = threadIdx.x; i2 < nr; i2 += blockDim.x) signs[i2] = Xn[i1 + Y1 * i2];
+    cp_async_wait<1>();  // the limbs
     __syncthreads();
     for (int i2 = warp; i2 < Y2; i2 += nw) {
         const int64_t i = i1 + Y1 * (int64_t)i2;
