@@ -280,6 +280,57 @@ def algorithmic_int_ops(info):
             OPS_BUTTERFLY * bf_i + OPS_SHOUP * mul_i]
 
 
+def stage_bits(logL: int):
+    """Radix exponents of the register stages of a length-2^logL transform
+    (at most 4 bits each, as even as possible, larger first)."""
+    nst = (logL + 3) // 4
+    if nst == 0:
+        return []
+    base, extra = logL // nst, logL % nst
+    return [base + (1 if i < extra else 0) for i in range(nst)]
+
+
+# INT8 mma.sync m16n8k32 throughput on a GB300, measured with a
+# microbenchmark (1216 blocks x 128 threads, eight independent accumulator
+# chains per warp, operands in registers): 151.0 Tops/s.  tcgen05.mma has no
+# 8-bit integer kind on sm_103a (ptxas rejects .kind::i8 for that target).
+INT8_MMA_SYNC_TOPS = 151.0
+
+
+def tensor_stage_ops(info, na: int, nb: int):
+    """INT8 tensor operations (2 per multiply-add) of the radix-16 stages of
+    one product under IPM_TENSOR_STAGES, per pass [forward (+outer),
+    middle, inverse (+outer)]: a stage vector of 16 elements costs 4 byte
+    slices x 2 K-chunks of 16 x 8 x 32 products shared by 8 vectors, i.e.
+    8192 operations (4096 when its upper half is zero)."""
+    r, Y, K = info["r"], info["Y"], info["K"]
+    Y1, Y2, Y1b = info["Y1"], info["Y2"], info["Y1b"]
+    lg = lambda x: int(x).bit_length() - 1  # noqa: E731
+    n16 = lambda logL: sum(1 for b in stage_bits(logL) if b == 4)  # noqa: E731
+    full = 8192
+    fwd = 0
+    for n in (na, nb):
+        fwd += n16(lg(K)) * (n * 2 * K // 16) * full          # x DFTs of the coefficient rows
+        sb = stage_bits(lg(Y2))
+        if sb:
+            i1 = np.arange(Y1)
+            nr = np.clip((n - i1 + Y1 - 1) // Y1, 0, Y2)
+            hz = int(np.count_nonzero((Y2 >= 2) & (2 * nr <= Y2)))
+            per_tile = Y2 * 2 * K // 16
+            for i, b in enumerate(sb):
+                if b == 4:
+                    cost = hz * 4096 + (Y1 - hz) * full if i == 0 else Y1 * full
+                    fwd += per_tile * cost
+    mid_bits = stage_bits(lg(Y1 // Y1b))
+    mid = 0
+    if len(mid_bits) >= 2:
+        k16 = sum(1 for b in mid_bits[:-1] if b == 4)
+        mid = 3 * k16 * (Y * 2 * K // 16) * full                # A and B forward, the product inverse
+    outer = n16(lg(Y1b)) * (Y * 2 * K // 16) * full if Y1b > 1 else 0
+    inv = n16(lg(Y2)) * (Y * 2 * K // 16) * full + n16(lg(K)) * (info["nc"] * 2 * K // 16) * full
+    return [r * (fwd + 2 * outer), r * mid, r * (inv + outer)]
+
+
 def alu_peak_tops(sm_mhz_max: float) -> float:
     """Integer issue peak: 152 SMs x 4 schedulers x 32 lanes, one 32-bit
     instruction per lane per cycle, at the maximum SM clock."""
@@ -501,6 +552,50 @@ def run_ours(args):
         del c2, cn2
     plain_plan.close()
 
+    # the same plan with every radix-16 stage on the INT8 tensor cores
+    # (IPM_TENSOR_STAGES), timed on the same inputs; its output must be
+    # byte-identical
+    tensor = None
+    if not args.no_tensor:
+        tplan = ipm.Plan(shape, flags=flags | ipm.IPM_TENSOR_STAGES)
+        c3, cn3 = tplan.empty_output()
+        for _ in range(max(1, args.warmup // 2)):
+            tplan.mul(da, dan, db, dbn, c3, cn3)
+        tplan.sync()
+        if not (torch.equal(c, c3) and torch.equal(cn, cn3)):
+            raise SystemExit("tensor-core stages and integer stages disagree")
+        tplan.set_profiling(True)
+        tm, tpass = [], np.zeros(3)
+        nt = max(3, args.steps // 2)
+        for _ in range(nt):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tplan.mul(da, dan, db, dbn, c3, cn3, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            tm.append(e0.elapsed_time(e1))
+            tpass += np.array(tplan.phase_ms())
+        tplan.set_profiling(False)
+        tplan.sync()
+        tpass /= nt
+        tops = tensor_stage_ops(tplan.info, sh.na, sh.nb)
+        t_ms = float(np.mean(tm))
+        tensor = {"ms_per_step": t_ms, "value": 1e3 / t_ms,
+                  "ratio_to_integer_stages": float(np.sum(step_ms) / args.steps) / t_ms,
+                  "passes_ms": {PASS_NAMES[i]: float(tpass[i]) for i in range(3)},
+                  "int8_tensor_ops": int(sum(tops)),
+                  "int8_tensor": {"achieved": sum(tops) / (t_ms / 1e3) / 1e12, "peak": INT8_MMA_SYNC_TOPS,
+                                  "unit": "Tops/s (int8, mma.sync)",
+                                  "frac": sum(tops) / (t_ms / 1e3) / 1e12 / INT8_MMA_SYNC_TOPS,
+                                  "k_middle_achieved": tops[1] / (tpass[1] / 1e3) / 1e12 if tpass[1] else None,
+                                  "peak_kind": "measured mma.sync m16n8k32 u8 microbenchmark"},
+                  "path": "IPM_TENSOR_STAGES: radix-16 stages as byte-slice u8 matrix products with "
+                          "int32 accumulation (mma.sync), exact Montgomery reduction; output byte-identical"}
+        del c3, cn3
+        tplan.close()
+
     local_ms = float(np.sum(step_ms))
     total_ms = max_over_ranks(dist, local_ms, dev)
     ms_per_step = total_ms / args.steps
@@ -598,6 +693,7 @@ def run_ours(args):
                        3 + (2 if info["Y1b"] > 1 else 0))},
         "roofline": roofline,
         "passes": passes,
+        "tensor_stages": tensor,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -624,6 +720,8 @@ def main(argv=None):
     ap.add_argument("--plain", action="store_true",
                     help="the plain path: analytic planner only, no learned dispatch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tensor", action="store_true",
+                    help="skip timing the tensor-core-stage variant beside the chosen form")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":

@@ -71,6 +71,16 @@ typedef enum {
                                  ipm_set_cost_model); ignored with params */
 #define IPM_GRAPH 4u          /* batched calls replay one CUDA graph of their
                                  grouped launches (see ipm_mul_batched) */
+#define IPM_TENSOR_STAGES 8u  /* every radix-16 transform stage runs as 8-bit
+                                 byte-slice matrix products with 32-bit
+                                 accumulation on the INT8 tensor cores
+                                 (mma.sync .u8), reduced exactly mod p;
+                                 bit-identical output.  Applies to products
+                                 launched one at a time (ipm_mul, the host-
+                                 buffer calls, batched products that run
+                                 alone); grouped batch launches keep the
+                                 integer stages.  A GPU formulation of the
+                                 DFTs of §2.1; the paper has no counterpart. */
 
 /* One product shape: a has deg_a+1 coefficients with |a_i| < 2^bits_a. */
 typedef struct {

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libipm.so")
 IPM_SYNC = 1
 IPM_COSTMODEL = 2
 IPM_GRAPH = 4
+IPM_TENSOR_STAGES = 8  # radix-16 stages on the INT8 tensor cores (see include/ipm.h)
 
 STATUS = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_BOUND", 3: "IPM_ERR_NOMEM",
           4: "IPM_ERR_CUDA", 5: "IPM_ERR_TIMEOUT", 6: "IPM_ERR_UNSUPPORTED"}
@@ -440,5 +441,5 @@ def to_host(c, c_neg):
 
 
 __all__ = ["Plan", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
-           "IPM_SYNC", "IPM_COSTMODEL", "IPM_GRAPH", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES", "candidates",
+           "IPM_SYNC", "IPM_COSTMODEL", "IPM_GRAPH", "IPM_TENSOR_STAGES", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES", "candidates",
            "mlp_train", "mlp_grad", "mlp_predict", "set_cost_model", "set_tuned", "dispatch"]

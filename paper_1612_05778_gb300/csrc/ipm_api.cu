@@ -312,6 +312,28 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
             sp.kp.pc[t].untw = blk + L.untw;
         }
     }
+    // IPM_TENSOR_STAGES: the radix-16 fragment tables, one set for every
+    // shape (prime t is the same for every shape: the r largest of the table)
+    if (flags & IPM_TENSOR_STAGES) {
+        const ShapePlan *wide = nullptr;
+        for (auto &sp : plan->shapes)
+            if (!sp.school && (!wide || sp.kp.r > wide->kp.r)) wide = &sp;
+        if (wide) {
+            for (auto &sp : plan->shapes)
+                for (int t = 0; !sp.school && t < sp.kp.r; ++t)
+                    if (sp.info.primes[t] != wide->info.primes[t]) { free_plan(plan); return IPM_ERR_UNSUPPORTED; }
+            std::vector<uint32_t> frag((size_t)wide->kp.r * TC_FRAG_WORDS);
+            build_tc_fragments(wide->info.primes, wide->kp.r, frag.data());
+            void *d = nullptr;
+            ce = cudaMalloc(&d, frag.size() * sizeof(uint32_t));
+            if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+            plan->allocations.push_back(d);
+            ce = cudaMemcpy(d, frag.data(), frag.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+            for (auto &sp : plan->shapes)
+                if (!sp.school) sp.kp.tcfrag = (const uint32_t *)d;
+        }
+    }
     // batched calls run a group's products at once: the workspace holds the
     // largest group (groups are cut at kBatchWorkspaceWords or one product)
     if (n > 1) zmax = std::max(zmax, batch_workspace_words(plan->shapes));

@@ -28,6 +28,11 @@ constexpr int THREADS_INV = 512;
 constexpr int THREADS_OUTER = 256;
 constexpr int OUTER_TILE_WORDS = 8192;  // outer-pass tile: Y1b rows x W words
 
+// Tensor-core radix-16 stage tables (IPM_TENSOR_STAGES): per prime, the A
+// fragments of the forward and of the inverse radix-16 DFT matrix in byte
+// slices (ntt_stages.cuh, stage_tc16), 1024 words each.
+constexpr int TC_FRAG_WORDS = 2048;
+
 // Device error word bits.
 constexpr int ERRBIT_BOUND = 1;      // an input coefficient >= 2^bits
 constexpr int ERRBIT_INTERNAL = 2;   // recombination top limb not a sign word
@@ -76,6 +81,9 @@ struct KParams {
     uint32_t *Z;          // workspace: r x 2 x Y x 2K words
     int *err;             // device error word
     int32_t batch_index;  // batched launches: index of this product's operands
+    // IPM_TENSOR_STAGES: r x TC_FRAG_WORDS fragment words (prime t at
+    // t * TC_FRAG_WORDS), or null for the integer stages
+    const uint32_t *tcfrag;
 };
 
 // Host-side plan record for one shape.
@@ -121,6 +129,10 @@ ipm_status dispatch_params(const ipm_shape *shapes, int32_t n, ipm_params *out, 
 // sp.table_words uint2 entries) and fills the scalar constants of sp.kp.
 void build_tables(ShapePlan &sp, uint2 *tab);
 
+// The tensor-core stage tables of primes[0..r) into out (r x TC_FRAG_WORDS
+// words).
+void build_tc_fragments(const uint32_t *primes, int r, uint32_t *out);
+
 // Table block offsets (uint2 entries) within one prime's block.
 struct TableLayout {
     size_t ty_f, ty_i, t1_f, t1_i, tx_f, tx_i, untw, total;
@@ -153,6 +165,14 @@ int launch_school(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, con
 // Products a batched call runs one at a time (split, packed or schoolbook).
 inline bool runs_alone(const ShapePlan &sp) { return sp.school || sp.kp.Y1b > 1 || sp.kr.s > 1; }
 int set_kernel_attributes();
+// The same passes with every radix-16 stage on the tensor cores
+// (ipm_kernels_tc.cu); the launchers above call these when kp.tcfrag is set.
+int set_kernel_attributes_tc();
+int launch_forward_tc(const KParams &kp, size_t smem, const uint32_t *a, const uint8_t *an,
+                      const uint32_t *b, const uint8_t *bn, void *stream);
+int launch_middle_tc(const KParams &kp, size_t smem, void *stream);
+int launch_inverse_tc(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, void *stream);
+int launch_outer_tc(const KParams &kp, size_t smem, bool forward, void *stream);
 
 // One group of a batched call: products that share the kernel variants,
 // launched as three ragged grids.  items[p][b] = (index into params, tile).

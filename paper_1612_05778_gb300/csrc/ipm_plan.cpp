@@ -544,6 +544,49 @@ void build_tables(ShapePlan &sp, uint2 *tab) {
     for (int i = 0; i < RMAX; ++i) kp.m_words[i] = i < kp.r ? mw[i] : 0;
 }
 
+// Byte-slice fragments of the radix-16 DFT matrices for the tensor-core
+// stages (layout and arithmetic: stage_tc16 in ntt_stages.cuh).  omega is
+// omega_16 = g^((p-1)/16) for the generator g every table of the plan uses,
+// so it is the root every radix-16 register stage uses too.
+void build_tc_fragments(const uint32_t *primes, int r, uint32_t *out) {
+    auto brev4 = [](int x) { return ((x & 1) << 3) | ((x & 2) << 1) | ((x & 4) >> 1) | ((x & 8) >> 3); };
+    for (int t = 0; t < r; ++t) {
+        const uint32_t p = primes[t];
+        const uint64_t w = root_of_unity(p, 4), wi = invmod((uint32_t)w, p);
+        uint64_t pw[16], pwi[16], cs[4];
+        pw[0] = pwi[0] = 1;
+        for (int e = 1; e < 16; ++e) {
+            pw[e] = pw[e - 1] * w % p;
+            pwi[e] = pwi[e - 1] * wi % p;
+        }
+        cs[0] = (1ull << 32) % p;  // 2^(8s) 2^32 mod p
+        for (int s = 1; s < 4; ++s) cs[s] = (cs[s - 1] << 8) % p;
+        for (int dir = 0; dir < 2; ++dir) {
+            uint32_t *frag = out + (size_t)t * TC_FRAG_WORDS + (size_t)dir * (TC_FRAG_WORDS / 2);
+            // C[j][k][s] = E[j][k] 2^(8s) 2^32 mod p
+            uint32_t C[16][16][4];
+            for (int j = 0; j < 16; ++j)
+                for (int k = 0; k < 16; ++k) {
+                    const uint64_t e = dir == 0 ? pw[(brev4(j) * k) & 15] : pwi[(j * brev4(k)) & 15];
+                    for (int s = 0; s < 4; ++s) C[j][k][s] = (uint32_t)(e * cs[s] % p);
+                }
+            for (int l = 0; l < 4; ++l)
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int g = lane >> 2, q = lane & 3;
+                    for (int c = 0; c < 2; ++c)
+                        for (int i = 0; i < 4; ++i) {
+                            // register i: rows g (i even) or g + 8 (i odd),
+                            // inputs 8c + q (i < 2) or 8c + 4 + q (i >= 2)
+                            const int j = g + 8 * (i & 1), k = 8 * c + q + 4 * (i >> 1);
+                            uint32_t word = 0;
+                            for (int s = 0; s < 4; ++s) word |= ((C[j][k][s] >> (8 * l)) & 0xffu) << (8 * s);
+                            frag[(l * 32 + lane) * 8 + c * 4 + i] = word;
+                        }
+                }
+        }
+    }
+}
+
 }  // namespace ipm
 
 namespace ipm {

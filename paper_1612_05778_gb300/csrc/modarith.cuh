@@ -34,6 +34,13 @@ __device__ __forceinline__ uint32_t montmul(uint32_t a, uint32_t b, uint32_t p, 
     return hi + mh + (lo != 0u);
 }
 
+// Montgomery REDC of a 64-bit V < p 2^32: V 2^-32 mod p in [0, 2p).
+__device__ __forceinline__ uint32_t redc64(uint64_t V, uint32_t p, uint32_t mont) {
+    const uint32_t lo = (uint32_t)V, hi = (uint32_t)(V >> 32);
+    const uint32_t m = lo * mont;
+    return hi + __umulhi(m, p) + (lo != 0u);
+}
+
 // Forward (DIF) butterfly: (x, y) -> (x + y, (x - y) w), inputs in [0, 2p).
 __device__ __forceinline__ void bf_dif(uint32_t &x, uint32_t &y, uint2 w, uint32_t p, uint32_t p2) {
     const uint32_t s = red(x + y, p2);

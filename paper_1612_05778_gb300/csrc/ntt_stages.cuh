@@ -280,6 +280,131 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Radix-16 stages on the INT8 tensor cores (IPM_TENSOR_STAGES).
+//
+// A radix-16 DFT over Z/p is the product of a 16 x 16 matrix E (powers of
+// omega_16; rows in the order the stage leaves its outputs: forward
+// E[m][k] = omega^{brev(m) k}, inverse E[n][m] = omega^{-n brev(m)}) with
+// each input vector x.  Split every input word into bytes,
+// x_k = sum_s x_k^(s) 2^(8s), and every constant C[j][k][s] =
+// E[j][k] 2^(8s) 2^32 mod p into bytes as well, C = sum_l C^(l) 2^(8l).
+// Then
+//     V_j = sum_l 2^(8l) D_l[j],  D_l[j] = sum_{k,s} C^(l)[j][k][s] x_k^(s),
+// is congruent to 2^32 sum_k E[j][k] x_k modulo p, and every D_l is the
+// product of a 16 x 64 byte matrix with the 64 bytes of x: an unsigned
+// 8-bit matrix product with 32-bit accumulation, exact because
+// D_l <= 64 * 255^2 < 2^22.  So V < 2^46 < p 2^32, and one Montgomery
+// reduction returns sum_k E[j][k] x_k mod p in [0, 2p): the same residue
+// the register stage computes, with no rounding anywhere.
+//
+// mma.sync m16n8k32 .u8: a warp multiplies 8 vectors at once.  Lane
+// (g, q) = (lane / 4, lane % 4) supplies, as its B fragment, words
+// x_{q + 4i} (i < 4) of vector g read straight from the tile -- the bytes
+// of a little-endian word are the K-dimension entries 4k + s in order --
+// and receives D_l[j] of vectors 2q, 2q + 1 for rows j = g, g + 8.  The A
+// fragments (the byte slices C^(l)) are precomputed per prime and
+// direction: word ((l * 32 + lane) * 8 + c * 4 + i) of a 1024-word table
+// is register i of K-chunk c (inputs 8c .. 8c + 7) of slice l.
+// ---------------------------------------------------------------------------
+
+struct NoTc {
+    static constexpr bool on = false;
+};
+// The fragment tables of one prime (forward and inverse matrix) and
+// -p^{-1} mod 2^32.
+struct TcOn {
+    static constexpr bool on = true;
+    const uint32_t *fwd, *inv;
+    uint32_t mont;
+};
+
+__device__ __forceinline__ void mma_u8_m16n8k32(uint32_t (&d)[4], uint4 a, uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k32.row.col.s32.u8.u8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// Group g of a stage: its first element's address, transform t, and n1.
+struct StageGroup {
+    uint32_t *base;
+    int t, n0, n1;  // n0: index of the group's first element in transform t
+};
+__device__ __forceinline__ StageGroup stage_group(const TileMap &M, int lT, int ltm, bool rot, int logLp, int logLc,
+                                                  int g) {
+    int rest;
+    uint32_t *tb = group_base(M, lT, ltm, g, rest);
+    if (rot) rest = rotate_rows(rest, M.rot);
+    const int n1 = rest & ((1 << logLp) - 1);
+    const int blk = rest >> logLp;
+    StageGroup G;
+    G.base = tb + ((blk << logLc) + n1) * M.es;
+    G.t = lT >= 0 ? (g & (M.T - 1)) : g % M.T;
+    G.n0 = (blk << logLc) + n1;
+    G.n1 = n1;
+    return G;
+}
+
+// One radix-16 stage (the same groups, twiddles and output order as
+// stage_dif<16> when FWD, stage_dit<16> otherwise) on the tensor cores.
+// HZ: inputs 8..15 of every group are zero (forward only): one K-chunk.
+template <bool FWD, bool HZ, bool SM, class In = TileIn, class Out = TileOut>
+__device__ __forceinline__ void stage_tc16(const TileMap &M, int logL, int logLc, const uint2 *__restrict__ tw,
+                                           int logT, uint32_t p, const TcOn &tc, const In &in = In(),
+                                           const Out &out = Out()) {
+    const int logLp = logLc - 4;
+    const int Lp = 1 << logLp;
+    const int total = M.T << (logL - 4);
+    const int tsh = logT - logLc;
+    const int lT = ilog2_if_pow2(M.T), ltm = ilog2_if_pow2(M.tm);
+    const int st = Lp * M.es;
+    const bool rot = M.rot && logLp >= 5;
+    const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    const uint4 *fr = reinterpret_cast<const uint4 *>(FWD ? tc.fwd : tc.inv) + 2 * lane;
+    for (int g0 = (int)(threadIdx.x >> 5) * 8; g0 < total; g0 += (int)(blockDim.x >> 5) * 8) {
+        uint32_t b[4] = {0u, 0u, 0u, 0u};
+        if (g0 + gq < total) {
+            const StageGroup G = stage_group(M, lT, ltm, rot, logLp, logLc, g0 + gq);
+            const uint32_t step = (uint32_t)G.n1 << tsh;
+#pragma unroll
+            for (int i = 0; i < (HZ ? 2 : 4); ++i) {
+                const int k = tq + 4 * i;
+                if (FWD)
+                    b[i] = G.base[k * st];
+                else if (Lp > 1)  // inverse: the twiddle omega_Lc^{-n1 brev(k)} first
+                    b[i] = shoup(G.base[k * st], tload<SM>(tw + step * bitrev((uint32_t)k, 4)), p);
+                else
+                    b[i] = in.get(G.base + k * st, G.t, G.n0 + k);
+            }
+        }
+        uint32_t d[4][4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            d[l][0] = d[l][1] = d[l][2] = d[l][3] = 0u;
+            mma_u8_m16n8k32(d[l], __ldg(fr + 64 * l), b[0], b[1]);
+            if (!HZ) mma_u8_m16n8k32(d[l], __ldg(fr + 64 * l + 1), b[2], b[3]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int g = g0 + 2 * tq + h;
+            if (g >= total) continue;
+            const StageGroup G = stage_group(M, lT, ltm, rot, logLp, logLc, g);
+            const uint32_t step = (uint32_t)G.n1 << tsh;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int m = gq + 8 * u, e = 2 * u + h;
+                const uint32_t lo = d[0][e] + (d[1][e] << 8);  // < 2^31
+                const uint32_t hi = d[2][e] + (d[3][e] << 8);
+                uint32_t v = redc64((uint64_t)hi * 65536u + lo, p, tc.mont);
+                if (FWD && Lp > 1) v = shoup(v, tload<SM>(tw + step * bitrev((uint32_t)m, 4)), p);
+                out.put(G.base + m * st, G.t, G.n0 + m * Lp, v);
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // Radix sequence: logL is split into ceil(logL/4) stages of at most 4 bits
 // (radix 16), as even as possible, the larger stages first.
 __device__ __forceinline__ void stage_split(int logL, int &nst, int &base, int &extra) {
@@ -288,10 +413,19 @@ __device__ __forceinline__ void stage_split(int logL, int &nst, int &base, int &
     extra = nst ? logL % nst : 0;
 }
 
-template <bool FWD, bool SM>
+template <bool FWD, bool SM, class TC = NoTc>
 __device__ __forceinline__ void run_stage(int b, const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
-                                          uint32_t p2, bool hz = false) {
+                                          uint32_t p2, bool hz = false, const TC &tc = TC()) {
+    if constexpr (TC::on) {
+        if (b == 4) {
+            if (FWD && hz)
+                stage_tc16<true, true, SM>(M, logL, logLc, tw, logT, p, tc);
+            else
+                stage_tc16<FWD, false, SM>(M, logL, logLc, tw, logT, p, tc);
+            return;
+        }
+    }
     if (FWD && hz) {
         switch (b) {
             case 1: stage_dif<2, SM, true>(M, logL, logLc, tw, logT, p, p2); return;
@@ -309,10 +443,19 @@ __device__ __forceinline__ void run_stage(int b, const TileMap &M, int logL, int
 }
 
 // The last stage of a forward transform, radix 2^b, writing through out.
-template <bool SM, class Out>
+template <bool SM, class Out, class TC = NoTc>
 __device__ __forceinline__ void last_stage_out(int b, bool hz, const TileMap &M, int logL, int logLc,
                                                const uint2 *__restrict__ tw, int logT, uint32_t p, uint32_t p2,
-                                               const Out &out) {
+                                               const Out &out, const TC &tc = TC()) {
+    if constexpr (TC::on) {
+        if (b == 4) {
+            if (hz)
+                stage_tc16<true, true, SM>(M, logL, logLc, tw, logT, p, tc, TileIn(), out);
+            else
+                stage_tc16<true, false, SM>(M, logL, logLc, tw, logT, p, tc, TileIn(), out);
+            return;
+        }
+    }
     if (hz) {
         switch (b) {
             case 1: stage_dif<2, SM, true>(M, logL, logLc, tw, logT, p, p2, out); return;
@@ -331,10 +474,10 @@ __device__ __forceinline__ void last_stage_out(int b, bool hz, const TileMap &M,
 
 // ntt_forward whose last stage hands every output to out.put instead of
 // writing it back to the tile (a length-1 transform hands over its input).
-template <bool SM = false, class Out>
+template <bool SM = false, class Out, class TC = NoTc>
 __device__ __forceinline__ void ntt_forward_out(const TileMap &M, int logL, const uint2 *__restrict__ tw,
                                                 int logT, uint32_t p, uint32_t p2, bool upper_zero,
-                                                const Out &out) {
+                                                const Out &out, const TC &tc = TC()) {
     int nst, base, extra;
     stage_split(logL, nst, base, extra);
     if (nst == 0) {
@@ -348,26 +491,27 @@ __device__ __forceinline__ void ntt_forward_out(const TileMap &M, int logL, cons
     int logLc = logL;
     for (int i = 0; i + 1 < nst; ++i) {
         const int b = base + (i < extra ? 1 : 0);
-        run_stage<true, SM>(b, M, logL, logLc, tw, logT, p, p2, upper_zero && i == 0);
+        run_stage<true, SM>(b, M, logL, logLc, tw, logT, p, p2, upper_zero && i == 0, tc);
         logLc -= b;
     }
     last_stage_out<SM>(base + (nst - 1 < extra ? 1 : 0), upper_zero && nst == 1, M, logL, logLc, tw, logT, p, p2,
-                       out);
+                       out, tc);
 }
 
 // Full forward transform of length 2^logL on every transform of the map
 // (natural order in, bit-reversed order out).  Values in [0, 2p).
 // upper_zero: the second half of every transform's input is zero and is
 // not read (the zero padding of an acyclic convolution).
-template <bool SM = false>
+template <bool SM = false, class TC = NoTc>
 __device__ __forceinline__ void ntt_forward(const TileMap &M, int logL, const uint2 *__restrict__ tw,
-                                            int logT, uint32_t p, uint32_t p2, bool upper_zero = false) {
+                                            int logT, uint32_t p, uint32_t p2, bool upper_zero = false,
+                                            const TC &tc = TC()) {
     int nst, base, extra;
     stage_split(logL, nst, base, extra);
     int logLc = logL;
     for (int i = 0; i < nst; ++i) {
         const int b = base + (i < extra ? 1 : 0);
-        run_stage<true, SM>(b, M, logL, logLc, tw, logT, p, p2, upper_zero && i == 0);
+        run_stage<true, SM>(b, M, logL, logLc, tw, logT, p, p2, upper_zero && i == 0, tc);
         logLc -= b;
     }
 }
@@ -423,11 +567,11 @@ __device__ __forceinline__ void stage_fused_pointwise(const TileMap &MA, const T
 // The last inverse stage hands its outputs to out.put; the return value says
 // whether it did (false when the transform has fewer than two stages: the
 // results are then in MA's tile).
-template <bool SM, bool COMPACT, typename WaitB, class Out = TileOut>
+template <bool SM, bool COMPACT, typename WaitB, class Out = TileOut, class TC = NoTc>
 __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &MB, int logL,
                                              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
                                              int logT, uint32_t p, uint32_t p2, uint32_t mont, WaitB wait_b,
-                                             const Out &out = Out()) {
+                                             const Out &out = Out(), const TC &tc = TC()) {
     int nst, base, extra;
     stage_split(logL, nst, base, extra);
     if (nst == 0) {  // length 1: the product of the single values
@@ -463,7 +607,7 @@ __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &M
         for (int i = 0; i + 1 < nst; ++i) {
             const int b = base + (i < extra ? 1 : 0);
             tables(tab, logLc, tf, ti, lg);
-            run_stage<true, SM>(b, M, logL, logLc, tf, lg, p, p2);
+            run_stage<true, SM>(b, M, logL, logLc, tf, lg, p, p2, false, tc);
             tab += 2 << logLc;
             logLc -= b;
         }
@@ -492,9 +636,15 @@ __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &M
         tab -= 2 << logLc;  // stage i's tables precede stage i+1's
         tables(tab, logLc, tf, ti, lg);
         if (i > 0) {
-            run_stage<false, SM>(b, MA, logL, logLc, ti, lg, p, p2);
+            run_stage<false, SM>(b, MA, logL, logLc, ti, lg, p, p2, false, tc);
         } else {  // the last inverse stage
             const TileIn in;
+            if constexpr (TC::on) {
+                if (b == 4) {
+                    stage_tc16<false, false, SM>(MA, logL, logLc, ti, lg, p, tc, in, out);
+                    continue;
+                }
+            }
             switch (b) {
                 case 1: stage_dit<2, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
                 case 2: stage_dit<4, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
@@ -508,24 +658,25 @@ __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &M
 
 // Inverse of ntt_forward up to the factor 2^logL (tw: inverse table): the
 // forward stages replayed backwards.
-template <bool SM = false>
+template <bool SM = false, class TC = NoTc>
 __device__ __forceinline__ void ntt_inverse(const TileMap &M, int logL, const uint2 *__restrict__ tw,
-                                            int logT, uint32_t p, uint32_t p2) {
+                                            int logT, uint32_t p, uint32_t p2, const TC &tc = TC()) {
     int nst, base, extra;
     stage_split(logL, nst, base, extra);
     int logLc = 0;
     for (int i = nst - 1; i >= 0; --i) {
         const int b = base + (i < extra ? 1 : 0);
         logLc += b;
-        run_stage<false, SM>(b, M, logL, logLc, tw, logT, p, p2);
+        run_stage<false, SM>(b, M, logL, logLc, tw, logT, p, p2, false, tc);
     }
 }
 
 // ntt_inverse whose first stage reads every input through in.get (a
 // length-1 transform writes in.get of its input back to the tile).
-template <bool SM = false, class In>
+template <bool SM = false, class In, class TC = NoTc>
 __device__ __forceinline__ void ntt_inverse_in(const TileMap &M, int logL, const uint2 *__restrict__ tw,
-                                               int logT, uint32_t p, uint32_t p2, const In &in) {
+                                               int logT, uint32_t p, uint32_t p2, const In &in,
+                                               const TC &tc = TC()) {
     int nst, base, extra;
     stage_split(logL, nst, base, extra);
     if (nst == 0) {
@@ -541,6 +692,12 @@ __device__ __forceinline__ void ntt_inverse_in(const TileMap &M, int logL, const
         const int b = base + (i < extra ? 1 : 0);
         logLc += b;
         if (i == nst - 1) {  // the first inverse stage (every twiddle is 1)
+            if constexpr (TC::on) {
+                if (b == 4) {
+                    stage_tc16<false, false, SM>(M, logL, logLc, tw, logT, p, tc, in);
+                    continue;
+                }
+            }
             switch (b) {
                 case 1: stage_dit<2, SM>(M, logL, logLc, tw, logT, p, p2, in); break;
                 case 2: stage_dit<4, SM>(M, logL, logLc, tw, logT, p, p2, in); break;
@@ -548,7 +705,7 @@ __device__ __forceinline__ void ntt_inverse_in(const TileMap &M, int logL, const
                 default: stage_dit<16, SM>(M, logL, logLc, tw, logT, p, p2, in); break;
             }
         } else {
-            run_stage<false, SM>(b, M, logL, logLc, tw, logT, p, p2);
+            run_stage<false, SM>(b, M, logL, logLc, tw, logT, p, p2, false, tc);
         }
     }
 }
