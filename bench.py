@@ -56,7 +56,8 @@ UNIT = "products/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 PASS_NAMES = ["k_forward", "k_middle", "k_inverse"]
-KERNEL_SRC = os.path.join(ROOT, "paper_1612_05778_gb300", "csrc", "ipm_kernels.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_1612_05778_gb300", "csrc", n)
+              for n in ("ipm_kernels.cu", "passes.cuh", "ntt_stages.cuh", "modarith.cuh", "ipm_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_large_dense.md")
 
 
@@ -346,8 +347,12 @@ def load_peak_hbm():
 
 
 def kernel_source_hash():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the sources the three pass kernels are compiled from."""
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str):
