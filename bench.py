@@ -464,6 +464,74 @@ def run_batch(args):
     return 0
 
 
+def run_taylor(args):
+    """Taylor shift by one, g(x) = f(x + 1), of 2^14 coefficients below
+    2^4096 (seed 5) through ipm_taylor_shift: shifts/s, inputs resident on
+    the device, L2 flushed between timed steps; the oracle's sampled
+    coefficients (g_k = sum_{i>=k} C(i,k) f_i, Python integers, one core)
+    scaled to a whole shift as the CPU baseline."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1612_05778_gb300 import build as ipm_build
+    ipm_build.build()
+    import paper_1612_05778_gb300 as ipm
+    (n, bits), f = W.taylor_dense(seed=5)
+    ts = ipm.TaylorShift(n, bits)
+    df, dfn = ipm.to_device(*f)
+    g = torch.empty((n, ts.limbs), dtype=torch.int32, device="cuda")
+    gn = torch.empty((n,), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ts.shift(df, dfn, g, gn)
+    ts.sync()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    l0 = ipm.launch_count()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ts.shift(df, dfn, g, gn, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = ipm.launch_count() - l0
+    clocks = sampler.stop()
+    ts.sync()
+    t_ms = float(np.mean(ms))
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle.taylor import taylor_coeff
+        F = [(-1 if s else 1) * int.from_bytes(row.tobytes(), "little") for row, s in zip(f[0], f[1])]
+        rng = np.random.default_rng(0)
+        done, work, t0 = 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            k = int(rng.integers(0, n))
+            taylor_coeff(F, k)
+            done += 1
+            work += n - k  # terms of g_k
+        dt = time.perf_counter() - t0
+        full = n * (n + 1) / 2
+        cpu = {"value": work / full / dt, "unit": "shifts/s", "cores": 1, "kind": "oracle",
+               "sample": "%d random output coefficients (%.3g%% of the shift's terms) in %.1f s on one core, "
+                         "scaled to one whole shift" % (done, 100 * work / full, dt)}
+    line = {"metric": "exact Taylor shifts f(x+1)/s", "value": 1e3 / t_ms, "unit": "shifts/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "taylor: n=16384 coefficients, |f_i| < 2^4096, signed uniform, seed 5",
+                       "output_limbs": ts.limbs, "levels": int(math.log2(n)),
+                       "l2": "flushed between timed steps (512 MiB write, outside the events)"},
+            "cpu_baseline": cpu, "gpu_launches": int(launches), "launches_per_step": launches / args.steps,
+            "clocks": clocks}
+    print(json.dumps(line))
+    ts.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -735,6 +803,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "taylor":
+        return run_taylor(args)
     return run_ours(args)
 
 

@@ -328,6 +328,35 @@ ipm_status ipm_mul_noalloc(const ipm_shape *shape, const uint32_t *a, const uint
 /* Wait for `stream`, then return and clear the plan's device error word. */
 ipm_status ipm_sync(ipm_plan_t plan, ipm_stream_t stream);
 
+/*
+ * Taylor shift by one: g(x) = f(x + 1), exactly, for f of degree `deg`
+ * with |f_i| < 2^bits -- the operation the paper's application (§1, real
+ * root isolation) builds on its product, there by the divide-and-conquer
+ * method (Algorithm E of von zur Gathen and Gerhard, ISSAC 1997).  Here:
+ * f padded to n' = 2^m coefficients; at level l (blocks of b = 2^l,
+ * already shifted) every pair of blocks (lo, hi) becomes lo + (x+1)^b hi,
+ * all pairs of a level in ONE ipm_mul of (x+1)^b by the hi blocks placed
+ * 2b apart; (x+1)^b is the square of (x+1)^(b/2) (ipm_mul); the block
+ * additions are sign-magnitude additions on the GPU.
+ *
+ * Layout: f and g as in ipm_mul (device pointers, sign-magnitude 32-bit
+ * limbs); f has stride ceil(bits/32), g has deg+1 coefficients with stride
+ * ipm_taylor_limbs() = ceil((bits + deg + 1)/32), since |g_k| <
+ * 2^(bits + deg + 1).  The plan owns its buffers and one ipm plan per level
+ * (flags IPM_COSTMODEL and IPM_TENSOR_STAGES pass to them; IPM_SYNC makes
+ * ipm_taylor_shift wait and return the device status).  Limits:
+ * deg < 2^20 and bits + 2^(m-1) <= 65536 (IPM_ERR_UNSUPPORTED).  Device
+ * errors (an input above its bound, IPM_ERR_BOUND; an internal bound
+ * violation, IPM_ERR_CUDA) are returned by ipm_taylor_sync.
+ */
+typedef struct ipm_taylor_s *ipm_taylor_t;
+ipm_status ipm_taylor_plan(ipm_taylor_t *out, int64_t deg, uint32_t bits, uint32_t flags);
+ipm_status ipm_taylor_limbs(ipm_taylor_t t, int32_t *limbs);
+ipm_status ipm_taylor_shift(ipm_taylor_t t, const uint32_t *f, const uint8_t *f_neg,
+                            uint32_t *g, uint8_t *g_neg, ipm_stream_t stream);
+ipm_status ipm_taylor_sync(ipm_taylor_t t, ipm_stream_t stream);
+ipm_status ipm_taylor_destroy(ipm_taylor_t t);
+
 /* Free a plan (waits for the device first).  NULL is accepted. */
 ipm_status ipm_destroy(ipm_plan_t plan);
 

@@ -111,6 +111,11 @@ def load_library(path: str | None = None):
     lib.ipm_set_cost_model.argtypes = [F32P, I32]
     lib.ipm_set_tuned.argtypes = [ctypes.POINTER(Shape), ctypes.POINTER(Params), I32]
     lib.ipm_dispatch.argtypes = [ctypes.POINTER(Shape), ctypes.POINTER(Params), ctypes.POINTER(I32)]
+    lib.ipm_taylor_plan.argtypes = [ctypes.POINTER(V), ctypes.c_int64, U32, U32]
+    lib.ipm_taylor_limbs.argtypes = [V, ctypes.POINTER(I32)]
+    lib.ipm_taylor_shift.argtypes = [V, V, V, V, V, V]
+    lib.ipm_taylor_sync.argtypes = [V, V]
+    lib.ipm_taylor_destroy.argtypes = [V]
     lib.ipm_strerror.argtypes = [ctypes.c_int]
     lib.ipm_strerror.restype = ctypes.c_char_p
     lib.ipm_launch_count.restype = ctypes.c_int64
@@ -118,7 +123,8 @@ def load_library(path: str | None = None):
                  "ipm_mul_host_async",
                  "ipm_mul_batched", "ipm_sync", "ipm_destroy", "ipm_set_profiling", "ipm_phase_ms",
                  "ipm_mul_noalloc", "ipm_mlp_train", "ipm_mlp_grad", "ipm_mlp_predict",
-                 "ipm_set_cost_model", "ipm_set_tuned", "ipm_dispatch"):
+                 "ipm_set_cost_model", "ipm_set_tuned", "ipm_dispatch", "ipm_taylor_plan", "ipm_taylor_limbs",
+                 "ipm_taylor_shift", "ipm_taylor_sync", "ipm_taylor_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -401,6 +407,45 @@ class Plan:
         _check(self._lib.ipm_sync(self._h, _stream_handle(stream)), "ipm_sync")
 
 
+class TaylorShift:
+    """g(x) = f(x + 1) for f with n coefficients below 2^bits in magnitude
+    (ipm_taylor_plan / ipm_taylor_shift): g has n coefficients of `limbs`
+    = ceil((bits + n) / 32) limbs."""
+
+    def __init__(self, n: int, bits: int, flags: int = 0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.ipm_taylor_plan(ctypes.byref(h), n - 1, bits, flags), "ipm_taylor_plan")
+        self._h, self._lib, self.n, self.bits = h, lib, n, bits
+        lg = ctypes.c_int32()
+        _check(lib.ipm_taylor_limbs(h, ctypes.byref(lg)), "ipm_taylor_limbs")
+        self.limbs = lg.value
+
+    def shift(self, f, f_neg, g=None, g_neg=None, stream=None):
+        import torch
+        if g is None or g_neg is None:
+            g = torch.empty((self.n, self.limbs), dtype=torch.int32, device="cuda")
+            g_neg = torch.empty((self.n,), dtype=torch.uint8, device="cuda")
+        args = [_dptr(f, torch.int32, (self.n, (self.bits + 31) // 32)), _dptr(f_neg, torch.uint8, (self.n,)),
+                _dptr(g, torch.int32, (self.n, self.limbs)), _dptr(g_neg, torch.uint8, (self.n,))]
+        _check(self._lib.ipm_taylor_shift(self._h, *args, _stream_handle(stream)), "ipm_taylor_shift")
+        return g, g_neg
+
+    def sync(self, stream=None):
+        _check(self._lib.ipm_taylor_sync(self._h, _stream_handle(stream)), "ipm_taylor_sync")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.ipm_taylor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # Size of the static device scratch of mul_noalloc (IPM_NOALLOC_SCRATCH_BYTES).
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -440,6 +485,6 @@ def to_host(c, c_neg):
     return (c.cpu().numpy().view(np.uint32), c_neg.cpu().numpy())
 
 
-__all__ = ["Plan", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
+__all__ = ["Plan", "TaylorShift", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
            "IPM_SYNC", "IPM_COSTMODEL", "IPM_GRAPH", "IPM_TENSOR_STAGES", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES", "candidates",
            "mlp_train", "mlp_grad", "mlp_predict", "set_cost_model", "set_tuned", "dispatch"]

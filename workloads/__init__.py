@@ -148,6 +148,13 @@ def huge_mixed(seed: int = 2, n: int = 262144, small_bits: int = 64, big_bits: i
     return Product(n, n, big_bits, big_bits), out[0], out[1]
 
 
+def taylor_dense(seed: int = 5, n: int = 16384, bits: int = 4096):
+    """Taylor-shift input: n random signed coefficients below 2^bits
+    (the shape of the root-isolation use in §1: dense, large coefficients)."""
+    rng = np.random.default_rng(seed)
+    return (n, bits), random_poly(rng, n, bits)
+
+
 def batch_shapes(seed: int = 3, count: int = 4096, dmin: int = 16, dmax: int = 8192,
                  bmin: int = 32, bmax: int = 4096):
     """Shapes for the batched workload: log-uniform degrees and bit bounds."""
