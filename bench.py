@@ -1,7 +1,7 @@
 """Benchmark: exact dense Z[y] products on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload large_dense|small_dense|large_all_ones|huge_dense|batch]
+                    [--workload large_dense|small_dense|large_all_ones|huge_dense|batch|taylor]
 
 One step is one whole product c = a*b (split, forward 2-D transforms over
 every prime, pointwise products, inverse transforms, CRT, recombination)
@@ -26,6 +26,12 @@ the learned dispatch, its grouped launches replayed as one CUDA graph, and,
 beside it, the same batch with the analytic planner and the same products
 as 4096 ipm_mul calls (the plain path);
 `speedup_vs_plain` is the ratio to the plain path.
+
+--workload taylor times ipm_taylor_shift, g(x) = f(x + 1), on 2^14
+coefficients below 2^4096 (seed 5), and prints its own line (shifts/s).
+
+Every default run also times the same product with the tensor-core radix-16
+stages (IPM_TENSOR_STAGES; `tensor_stages` in the line, --no-tensor skips it).
 
 Multi-GPU (torchrun): products are independent, so every rank multiplies its
 own pair (weak scaling, no data-path collective); the host-side barrier and
