@@ -1,7 +1,7 @@
 """Benchmark: exact dense Z[y] products on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload large_dense|small_dense|large_all_ones|huge_dense|batch|taylor]
+                    [--workload large_dense|small_dense|large_all_ones|huge_dense|batch|taylor|paper_table]
 
 One step is one whole product c = a*b (split, forward 2-D transforms over
 every prime, pointwise products, inverse transforms, CRT, recombination)
@@ -26,6 +26,9 @@ the learned dispatch, its grouped launches replayed as one CUDA graph, and,
 beside it, the same batch with the analytic planner and the same products
 as 4096 ipm_mul calls (the plain path);
 `speedup_vs_plain` is the ratio to the plain path.
+
+--workload paper_table times the shapes of the paper's own table (d = N =
+2^9 .. 2^16) and lists the paper's 48-core CVL_p^2 seconds beside each row.
 
 --workload taylor times ipm_taylor_shift, g(x) = f(x + 1), on 2^14
 coefficients below 2^4096 (seed 5), and prints its own line (shifts/s).
@@ -538,6 +541,82 @@ def run_taylor(args):
     return 0
 
 
+# The paper's own benchmark (§4, Table classical4andCVL2): random dense
+# polynomials with degree d equal to the coefficient size N, CVL_p^2 on a
+# 48-core AMD Opteron 6168 (900 MHz), seconds per product.  Context only:
+# another machine, another precision of primes.
+PAPER_CVL2_SECONDS = {9: 0.152, 10: 0.139, 11: 0.196, 12: 0.295, 13: 0.699, 14: 1.927, 15: 9.138, 16: 33.04}
+
+
+def run_paper_table(args):
+    """The paper's table shapes: d = N = 2^9 .. 2^16 (two polynomials of
+    2^k coefficients below 2^(2^k), signed uniform, seed k), each product
+    timed through ipm_mul with the plan the learned dispatch picks (the
+    planner's where the sweep did not reach); one JSON line whose value is
+    the largest shape's products/s, every row with the paper's time beside
+    it as context."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1612_05778_gb300 import build as ipm_build
+    ipm_build.build()
+    import paper_1612_05778_gb300 as ipm
+    from paper_1612_05778_gb300 import costmodel as cmod
+    cmod.install(points=cmod.load_sweep()["points"])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    l0 = ipm.launch_count()
+    for k in sorted(PAPER_CVL2_SECONDS):
+        d = 1 << k
+        rng = np.random.default_rng(k)
+        a = W.random_poly(rng, d, d)
+        b = W.random_poly(rng, d, d)
+        plan = ipm.Plan((d, d, d, d), flags=ipm.IPM_COSTMODEL)
+        da, dan = ipm.to_device(*a)
+        db, dbn = ipm.to_device(*b)
+        c, cn = plan.empty_output()
+        for _ in range(args.warmup):
+            plan.mul(da, dan, db, dbn, c, cn)
+        plan.sync()
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.mul(da, dan, db, dbn, c, cn, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        plan.sync()
+        t = float(np.mean(ms))
+        info = plan.info
+        rows.append({"d": d, "N": d, "ms": t, "products_per_s": 1e3 / t,
+                     "output_gbit_s": info["nc"] * info["lc"] * 32 / (t / 1e3) / 1e9,
+                     "plan": {x: info[x] for x in ("K", "M", "r", "Y", "Y2", "S", "Y1b", "kron", "school")},
+                     "paper_cvl2_s": PAPER_CVL2_SECONDS[k],
+                     "ratio_to_paper": PAPER_CVL2_SECONDS[k] / (t / 1e3)})
+        plan.close()
+        del da, dan, db, dbn, c, cn
+        torch.cuda.empty_cache()
+    launches = ipm.launch_count() - l0
+    clocks = sampler.stop()
+    top = rows[-1]
+    line = {"metric": METRIC, "value": top["products_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": top["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "paper_table: d = N = 2^9..2^16 (the paper's Table classical4andCVL2 shapes), "
+                                   "signed uniform, seed k; value = d = N = 2^16",
+                       "l2": "flushed between timed steps (512 MiB write, outside the events)",
+                       "paper_hardware": "48-core AMD Opteron 6168 at 900 MHz, CVL_p^2 (context only)"},
+            "rows": rows, "gpu_launches": int(launches), "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -811,6 +890,8 @@ def main(argv=None):
         return run_batch(args)
     if args.workload == "taylor":
         return run_taylor(args)
+    if args.workload == "paper_table":
+        return run_paper_table(args)
     return run_ours(args)
 
 

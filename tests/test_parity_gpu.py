@@ -365,3 +365,27 @@ def test_naturally_split_wide_product():
     want = oracle.coeffs(ks, a, b, sh.lc)
     assert_same((got[0][ks], got[1][ks]), want)
     _whole_output_identities(a, b, got)
+
+
+# ---- the paper's own table shapes (d = N = 2^k) ----------------------------
+
+@pytest.mark.parametrize("k", [9, 10, 11, 12, 13, 14, 15, 16])
+def test_paper_table_shapes(k):
+    """Random dense polynomials with degree d equal to the coefficient size N
+    (the shapes of the paper's Table classical4andCVL2), seed k: sampled
+    coefficients against the oracle where it finishes in seconds (k <= 13),
+    and for every k the exact identity c(t) = a(t) b(t) modulo three 61-bit
+    primes at random points."""
+    d = 1 << k
+    rng = np.random.default_rng(k)
+    a = W.random_poly(rng, d, d)
+    b = W.random_poly(rng, d, d)
+    got, info = gpu_mul(a, b, d, d)
+    nc = 2 * d - 1
+    if k <= 13:
+        ks = [0, 1, d - 1, d, nc - 1] + np.random.default_rng(nc).integers(0, nc, 2).tolist()
+        assert_same((got[0][ks], got[1][ks]), oracle.coeffs(ks, a, b, info["lc"]))
+    rng2 = np.random.default_rng(100 + k)
+    for q in CHECK_PRIMES:
+        t = int(rng2.integers(2, 2**60))
+        assert oracle.eval_mod(got, t, q) == oracle.eval_mod(a, t, q) * oracle.eval_mod(b, t, q) % q
