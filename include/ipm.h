@@ -62,7 +62,8 @@ typedef enum {
     IPM_ERR_NOMEM = 3,        /* device or host allocation failed */
     IPM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
     IPM_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
-    IPM_ERR_UNSUPPORTED = 6   /* shape outside what the plan tables support */
+    IPM_ERR_UNSUPPORTED = 6,  /* shape outside what the plan tables support */
+    IPM_ERR_MISMATCH = 7      /* a validated product failed its random check */
 } ipm_status;
 
 /* Plan flags. */
@@ -81,6 +82,11 @@ typedef enum {
                                  alone); grouped batch launches keep the
                                  integer stages.  A GPU formulation of the
                                  DFTs of §2.1; the paper has no counterpart. */
+#define IPM_VALIDATE 16u      /* every product of ipm_mul / the host-buffer
+                                 calls is checked on the GPU after it runs
+                                 (ipm_validate's test at a fresh random point);
+                                 a failure is returned as IPM_ERR_MISMATCH by
+                                 ipm_sync.  Batched calls are not checked. */
 
 /* One product shape: a has deg_a+1 coefficients with |a_i| < 2^bits_a. */
 typedef struct {
@@ -324,6 +330,20 @@ ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n,
 ipm_status ipm_mul_noalloc(const ipm_shape *shape, const uint32_t *a, const uint8_t *a_neg,
                            const uint32_t *b, const uint8_t *b_neg,
                            uint32_t *c, uint8_t *c_neg, ipm_stream_t stream);
+
+/*
+ * Randomised check of a finished product (no counterpart in the paper):
+ * evaluates a, b and c at one point t derived from `seed` modulo the
+ * Mersenne prime q = 2^61 - 1 on the GPU and compares c(t) with a(t) b(t).
+ * A c that differs from the exact product a*b in any limb or sign passes
+ * with probability at most deg(c) / q < 2^-40 (Schwartz-Zippel); the exact
+ * product always passes.  Layouts as in ipm_mul for `shape` (device
+ * pointers).  Waits for `stream`; returns IPM_OK or IPM_ERR_MISMATCH.
+ * Allocates and frees a few KB of device memory per call.
+ */
+ipm_status ipm_validate(const ipm_shape *shape, const uint32_t *a, const uint8_t *a_neg,
+                        const uint32_t *b, const uint8_t *b_neg,
+                        const uint32_t *c, const uint8_t *c_neg, uint64_t seed, ipm_stream_t stream);
 
 /* Wait for `stream`, then return and clear the plan's device error word. */
 ipm_status ipm_sync(ipm_plan_t plan, ipm_stream_t stream);

@@ -20,9 +20,10 @@ IPM_SYNC = 1
 IPM_COSTMODEL = 2
 IPM_GRAPH = 4
 IPM_TENSOR_STAGES = 8  # radix-16 stages on the INT8 tensor cores (see include/ipm.h)
+IPM_VALIDATE = 16      # every single product checked at a random point mod 2^61 - 1
 
 STATUS = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_BOUND", 3: "IPM_ERR_NOMEM",
-          4: "IPM_ERR_CUDA", 5: "IPM_ERR_TIMEOUT", 6: "IPM_ERR_UNSUPPORTED"}
+          4: "IPM_ERR_CUDA", 5: "IPM_ERR_TIMEOUT", 6: "IPM_ERR_UNSUPPORTED", 7: "IPM_ERR_MISMATCH"}
 
 
 class IpmError(RuntimeError):
@@ -111,6 +112,7 @@ def load_library(path: str | None = None):
     lib.ipm_set_cost_model.argtypes = [F32P, I32]
     lib.ipm_set_tuned.argtypes = [ctypes.POINTER(Shape), ctypes.POINTER(Params), I32]
     lib.ipm_dispatch.argtypes = [ctypes.POINTER(Shape), ctypes.POINTER(Params), ctypes.POINTER(I32)]
+    lib.ipm_validate.argtypes = [ctypes.POINTER(Shape), V, V, V, V, V, V, ctypes.c_uint64, V]
     lib.ipm_taylor_plan.argtypes = [ctypes.POINTER(V), ctypes.c_int64, U32, U32]
     lib.ipm_taylor_limbs.argtypes = [V, ctypes.POINTER(I32)]
     lib.ipm_taylor_shift.argtypes = [V, V, V, V, V, V]
@@ -123,7 +125,7 @@ def load_library(path: str | None = None):
                  "ipm_mul_host_async",
                  "ipm_mul_batched", "ipm_sync", "ipm_destroy", "ipm_set_profiling", "ipm_phase_ms",
                  "ipm_mul_noalloc", "ipm_mlp_train", "ipm_mlp_grad", "ipm_mlp_predict",
-                 "ipm_set_cost_model", "ipm_set_tuned", "ipm_dispatch", "ipm_taylor_plan", "ipm_taylor_limbs",
+                 "ipm_set_cost_model", "ipm_set_tuned", "ipm_dispatch", "ipm_validate", "ipm_taylor_plan", "ipm_taylor_limbs",
                  "ipm_taylor_shift", "ipm_taylor_sync", "ipm_taylor_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -472,6 +474,25 @@ def mul_noalloc(na: int, nb: int, bits_a: int, bits_b: int, a, a_neg, b, b_neg, 
     return c, c_neg
 
 
+def validate(na: int, nb: int, bits_a: int, bits_b: int, a, a_neg, b, b_neg, c, c_neg, seed: int = 1,
+             stream=None) -> bool:
+    """ipm_validate: True when c(t) = a(t) b(t) modulo 2^61 - 1 at the
+    point `seed` selects (always for the exact product; a wrong c passes
+    with probability < 2^-40).  CUDA tensors as for Plan.mul; waits."""
+    import torch
+    lib = load_library()
+    la, lb = (bits_a + 31) // 32, (bits_b + 31) // 32
+    args = [_dptr(a, torch.int32, (na, la)), _dptr(a_neg, torch.uint8, (na,)),
+            _dptr(b, torch.int32, (nb, lb)), _dptr(b_neg, torch.uint8, (nb,)),
+            _dptr(c, torch.int32), _dptr(c_neg, torch.uint8, (na + nb - 1,))]
+    st = lib.ipm_validate(ctypes.byref(Shape(na - 1, nb - 1, bits_a, bits_b)), *args,
+                          ctypes.c_uint64(seed), _stream_handle(stream))
+    if st == 7:
+        return False
+    _check(st, "ipm_validate")
+    return True
+
+
 def to_device(limbs: np.ndarray, neg: np.ndarray):
     """numpy (uint32 limbs, uint8 signs) -> CUDA tensors (int32 view, uint8)."""
     import torch
@@ -486,5 +507,5 @@ def to_host(c, c_neg):
 
 
 __all__ = ["Plan", "TaylorShift", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
-           "IPM_SYNC", "IPM_COSTMODEL", "IPM_GRAPH", "IPM_TENSOR_STAGES", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES", "candidates",
+           "IPM_SYNC", "IPM_COSTMODEL", "IPM_GRAPH", "IPM_TENSOR_STAGES", "IPM_VALIDATE", "validate", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES", "candidates",
            "mlp_train", "mlp_grad", "mlp_predict", "set_cost_model", "set_tuned", "dispatch"]

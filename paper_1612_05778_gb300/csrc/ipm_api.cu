@@ -30,6 +30,10 @@ struct ipm_plan_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int graph_kernels = 0;
+    // IPM_VALIDATE: partial sums of the evaluation check, and a call counter
+    // that gives every check its own point
+    uint64_t *val_part = nullptr;
+    uint64_t val_calls = 0;
     // per-pass profiling events (ipm_set_profiling)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool profiling = false;
@@ -57,8 +61,8 @@ void free_plan(ipm_plan_s *p) {
 
 bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
-ipm_status run_one(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a, const uint8_t *an,
-                   const uint32_t *b, const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream) {
+ipm_status run_product(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a, const uint8_t *an,
+                       const uint32_t *b, const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream) {
     if (!a || !an || !b || !bn || !c || !cn) return IPM_ERR_ARG;
     if (!aligned16(a) || !aligned16(b) || !aligned16(c)) return IPM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -82,6 +86,16 @@ ipm_status run_one(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a, con
     return IPM_OK;
 }
 
+// One product, then (IPM_VALIDATE) its randomised check at a fresh point.
+ipm_status run_one(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a, const uint8_t *an,
+                   const uint32_t *b, const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream) {
+    const ipm_status st = run_product(plan, sp, a, an, b, bn, c, cn, stream);
+    if (st != IPM_OK || !(plan->flags & IPM_VALIDATE)) return st;
+    const uint64_t t = validation_point(0x1612057780000000ull + plan->val_calls++);
+    return launch_validate(sp.info, a, an, b, bn, c, cn, t, plan->val_part, plan->err, stream) ? IPM_ERR_CUDA
+                                                                                                : IPM_OK;
+}
+
 ipm_status read_error(ipm_plan_s *plan, void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -92,6 +106,7 @@ ipm_status read_error(ipm_plan_s *plan, void *stream) {
         e = cudaMemset(plan->err, 0, sizeof(int));
         if (e != cudaSuccess) return cuda_status(e);
         if (h & ERRBIT_BOUND) return IPM_ERR_BOUND;
+        if (h & ERRBIT_MISMATCH) return IPM_ERR_MISMATCH;
         return IPM_ERR_CUDA;
     }
     return IPM_OK;
@@ -353,6 +368,12 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
         sp.kp.Z = plan->Z;
         sp.kp.err = plan->err;
     }
+    if (flags & IPM_VALIDATE) {
+        ce = cudaMalloc(&d, 3 * VAL_BLOCKS * sizeof(uint64_t));
+        if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+        plan->allocations.push_back(d);
+        plan->val_part = (uint64_t *)d;
+    }
     if (n > 1) {
         ipm_status st = build_batch(plan);
         if (st != IPM_OK) { free_plan(plan); return st; }
@@ -505,6 +526,7 @@ const char *ipm_strerror(ipm_status s) {
         case IPM_ERR_CUDA: return "CUDA error";
         case IPM_ERR_TIMEOUT: return "device wait timed out";
         case IPM_ERR_UNSUPPORTED: return "shape not supported";
+        case IPM_ERR_MISMATCH: return "product failed its randomised check";
     }
     return "unknown status";
 }

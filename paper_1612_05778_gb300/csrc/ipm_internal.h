@@ -36,6 +36,12 @@ constexpr int TC_FRAG_WORDS = 2048;
 // Device error word bits.
 constexpr int ERRBIT_BOUND = 1;      // an input coefficient >= 2^bits
 constexpr int ERRBIT_INTERNAL = 2;   // recombination top limb not a sign word
+constexpr int ERRBIT_MISMATCH = 4;   // IPM_VALIDATE: c(t) != a(t) b(t) mod 2^61 - 1
+
+// Randomised product check (ipm_validate.cu): blocks and threads of the
+// evaluation kernels; the scratch holds 3 x VAL_BLOCKS partial sums.
+constexpr int VAL_BLOCKS = 1216;  // 8 per SM: 64 warps in flight
+constexpr int VAL_THREADS = 256;
 
 // Per-prime constants.  Twiddle tables hold (w, floor(w * 2^32 / p)) pairs
 // for Shoup's precomputed-quotient multiplication.
@@ -165,6 +171,12 @@ int launch_school(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, con
 // Products a batched call runs one at a time (split, packed or schoolbook).
 inline bool runs_alone(const ShapePlan &sp) { return sp.school || sp.kp.Y1b > 1 || sp.kr.s > 1; }
 int set_kernel_attributes();
+// Evaluation point for a seed, and the check c(t) = a(t) b(t) mod 2^61 - 1
+// of one product laid out as I describes (ERRBIT_MISMATCH into *err).
+uint64_t validation_point(uint64_t seed);
+int launch_validate(const ipm_plan_info &I, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                    const uint8_t *bn, const uint32_t *c, const uint8_t *cn, uint64_t t, uint64_t *part, int *err,
+                    void *stream);
 // The same passes with every radix-16 stage on the tensor cores
 // (ipm_kernels_tc.cu); the launchers above call these when kp.tcfrag is set.
 int set_kernel_attributes_tc();
