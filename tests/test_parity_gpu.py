@@ -389,3 +389,35 @@ def test_paper_table_shapes(k):
     for q in CHECK_PRIMES:
         t = int(rng2.integers(2, 2**60))
         assert oracle.eval_mod(got, t, q) == oracle.eval_mod(a, t, q) * oracle.eval_mod(b, t, q) % q
+
+
+# ---- the supported maxima ------------------------------------------------------
+
+@pytest.mark.parametrize("n,bits", [(1 << 20, 32), (1 << 20, 1024)])
+def test_maximum_degree(n, bits):
+    """2^20 coefficients per operand: the product's y transform has length
+    Y = 2^21, the largest order the primes' roots of unity allow."""
+    rng = np.random.default_rng(n + bits)
+    a = W.random_poly(rng, n, bits)
+    b = W.random_poly(rng, n, bits)
+    got, info = gpu_mul(a, b, bits, bits)
+    assert info["Y"] == 1 << 21
+    nc = 2 * n - 1
+    ks = [0, 1, n - 1, n, nc - 2, nc - 1] + np.random.default_rng(nc).integers(0, nc, 2).tolist()
+    assert_same((got[0][ks], got[1][ks]), oracle.coeffs(ks, a, b, info["lc"]))
+    if bits <= 32:  # C(+-1) = A(+-1) B(+-1) with Python integers (cheap at 32 bits)
+        _whole_output_identities(a, b, got)
+    rng2 = np.random.default_rng(7)
+    for q in CHECK_PRIMES:
+        t = int(rng2.integers(2, 2**60))
+        assert oracle.eval_mod(got, t, q) == oracle.eval_mod(a, t, q) * oracle.eval_mod(b, t, q) % q
+
+
+@pytest.mark.parametrize("na,nb,ba,bb", [(4, 3, 65536, 65536), (37, 20, 65536, 1), (1, 1, 65536, 65536)])
+def test_maximum_bits(na, nb, ba, bb):
+    """Coefficients of the largest supported size (65536 bits): whole
+    outputs against the oracle."""
+    rng = np.random.default_rng(na * nb)
+    a = W.random_poly(rng, na, ba)
+    b = W.random_poly(rng, nb, bb)
+    check_vs_oracle(a, b, ba, bb)
