@@ -1,7 +1,7 @@
 """Benchmark: exact dense Z[y] products on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload large_dense|small_dense|large_all_ones|huge_dense|batch|taylor|paper_table]
+                    [--workload large_dense|small_dense|large_all_ones|huge_dense|huge_mixed|batch|taylor|paper_table]
 
 One step is one whole product c = a*b (split, forward 2-D transforms over
 every prime, pointwise products, inverse transforms, CRT, recombination)
@@ -83,6 +83,9 @@ def workload(name: str):
     if name == "huge_dense":
         sh, a, b = W.huge_dense(seed=2)
         return "huge_dense: d=262144, |coeff| < 2^1024, signed uniform, seed 2", sh, a, b
+    if name == "huge_mixed":
+        sh, a, b = W.huge_mixed(seed=2)
+        return ("huge_mixed: d=262144, half the positions < 2^64, the rest < 2^2048, signed, seed 2", sh, a, b)
     raise SystemExit("unknown workload " + name)
 
 

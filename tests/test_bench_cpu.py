@@ -1,0 +1,49 @@
+"""bench.py's accounting, on CPU: the models the roofline and the tensor
+figures are computed from, pinned to what the GPU counters measured.
+
+* tensor_stage_ops / 8192 is the number of mma.sync m16n8k32 instructions
+  the tensor-core stages issue; ncu counted, for one large_dense product
+  (profiles/ncu_tensor_stages_large_dense.md),
+  sm__inst_executed_pipe_tensor_subpipe_imma = 3,145,728 (forward),
+  18,874,368 (middle) and 3,145,680 (inverse).
+* algorithmic_bytes: the DRAM bytes every pass must move; ncu's DRAM reads
+  of the middle and inverse passes (profiles/traffic_large_dense.md:
+  402.85 MB and 203.37 MB) match the reads the model assigns them
+  (2 r Y 2K words, r Y 2K words plus tables).
+* stage_bits follows the radix split of the stage code (at most 4 bits a
+  stage, as even as possible, larger stages first).
+"""
+import pytest
+
+import bench
+import paper_1612_05778_gb300 as ipm
+
+
+@pytest.fixture(scope="module")
+def large_dense_info():
+    return ipm.choose(32768, 32768, 4096, 4096, K=128)
+
+
+def test_tensor_stage_model_matches_imma_counter(large_dense_info):
+    ops = bench.tensor_stage_ops(large_dense_info, 32768, 32768)
+    assert [o // 8192 for o in ops] == [3145728, 18874368, 3145680]
+    assert all(o % 8192 == 0 for o in ops)
+
+
+def test_algorithmic_bytes_match_measured_reads(large_dense_info):
+    fwd, mid, inv = bench.algorithmic_bytes(large_dense_info)
+    I = large_dense_info
+    z = I["r"] * I["Y"] * 2 * I["K"] * 4
+    assert mid == 3 * z
+    # measured DRAM reads: the middle pass reads both operands' transforms,
+    # the inverse pass the product's
+    assert abs(402.850304e6 - 2 * z) / (2 * z) < 0.002
+    assert abs(203.371008e6 - z) / z < 0.02
+    assert fwd > 2 * z and inv > z
+
+
+@pytest.mark.parametrize("logL,want", [(0, []), (1, [1]), (4, [4]), (5, [3, 2]), (7, [4, 3]), (8, [4, 4]),
+                                       (9, [3, 3, 3]), (11, [4, 4, 3]), (12, [4, 4, 4]), (21, [4, 4, 4, 3, 3, 3])])
+def test_stage_bits(logL, want):
+    assert bench.stage_bits(logL) == want
+    assert sum(want) == logL
