@@ -82,11 +82,13 @@ typedef enum {
                                  alone); grouped batch launches keep the
                                  integer stages.  A GPU formulation of the
                                  DFTs of §2.1; the paper has no counterpart. */
-#define IPM_VALIDATE 16u      /* every product of ipm_mul / the host-buffer
-                                 calls is checked on the GPU after it runs
-                                 (ipm_validate's test at a fresh random point);
-                                 a failure is returned as IPM_ERR_MISMATCH by
-                                 ipm_sync.  Batched calls are not checked. */
+#define IPM_VALIDATE 16u      /* every product is checked on the GPU after it
+                                 runs (ipm_validate's test: at a fresh random
+                                 point for ipm_mul and the host-buffer calls,
+                                 at the plan's fixed random point, in two
+                                 launches for all products, for batched
+                                 calls); a failure is returned as
+                                 IPM_ERR_MISMATCH by ipm_sync. */
 
 /* One product shape: a has deg_a+1 coefficients with |a_i| < 2^bits_a. */
 typedef struct {

@@ -34,6 +34,7 @@ struct ipm_plan_s {
     // that gives every check its own point
     uint64_t *val_part = nullptr;
     uint64_t val_calls = 0;
+    ValBatch vb;  // batched calls: the work list of their check (fixed point)
     // per-pass profiling events (ipm_set_profiling)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool profiling = false;
@@ -207,6 +208,56 @@ ipm_status capture_batch(ipm_plan_s *plan) {
     return IPM_OK;
 }
 
+// IPM_VALIDATE on a batched plan: items of up to VAL_ROWS rows of every
+// operand of every product, each weighted by t^row0 for the plan's point t.
+ipm_status build_val_batch(ipm_plan_s *plan) {
+    const auto &shapes = plan->shapes;
+    const uint64_t t = validation_point(0x5eed000000000000ull ^ (uint64_t)shapes.size());
+    const uint64_t tR = pow61_host(t, VAL_ROWS);
+    std::vector<ValItem> items;
+    std::vector<int64_t> first;
+    for (size_t i = 0; i < shapes.size(); ++i) {
+        const ipm_plan_info &I = shapes[i].info;
+        const int64_t rows[3] = {I.na, I.nb, I.nc};
+        const int32_t limbs[3] = {I.la, I.lb, I.lc};
+        for (int o = 0; o < 3; ++o) {
+            first.push_back((int64_t)items.size());
+            uint64_t w = 1;  // t^row0
+            for (int64_t r0 = 0; r0 < rows[o]; r0 += VAL_ROWS) {
+                ValItem it{};
+                it.product = (int32_t)i;
+                it.operand = o;
+                it.row0 = r0;
+                it.rows = (int32_t)std::min<int64_t>(VAL_ROWS, rows[o] - r0);
+                it.limbs = limbs[o];
+                it.t_row0 = w;
+                items.push_back(it);
+                w = (uint64_t)(((unsigned __int128)w * tR) % (((uint64_t)1 << 61) - 1));
+            }
+        }
+    }
+    first.push_back((int64_t)items.size());
+    cudaError_t ce;
+    void *d = nullptr;
+    if ((ce = cudaMalloc(&d, items.size() * sizeof(ValItem))) != cudaSuccess) return cuda_status(ce);
+    plan->allocations.push_back(d);
+    if ((ce = cudaMemcpy(d, items.data(), items.size() * sizeof(ValItem), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_status(ce);
+    plan->vb.items = (const ValItem *)d;
+    if ((ce = cudaMalloc(&d, first.size() * sizeof(int64_t))) != cudaSuccess) return cuda_status(ce);
+    plan->allocations.push_back(d);
+    if ((ce = cudaMemcpy(d, first.data(), first.size() * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_status(ce);
+    plan->vb.first = (const int64_t *)d;
+    if ((ce = cudaMalloc(&d, items.size() * sizeof(uint64_t))) != cudaSuccess) return cuda_status(ce);
+    plan->allocations.push_back(d);
+    plan->vb.part = (uint64_t *)d;
+    plan->vb.nitems = (int64_t)items.size();
+    plan->vb.nproducts = (int32_t)shapes.size();
+    plan->vb.t = t;
+    return IPM_OK;
+}
+
 ipm_status build_batch(ipm_plan_s *plan) {
     const auto &shapes = plan->shapes;
     cudaError_t ce;
@@ -376,6 +427,7 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
     }
     if (n > 1) {
         ipm_status st = build_batch(plan);
+        if (st == IPM_OK && (flags & IPM_VALIDATE)) st = build_val_batch(plan);
         if (st != IPM_OK) { free_plan(plan); return st; }
     }
     *out = plan;
@@ -477,6 +529,8 @@ ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n, 
             const ipm_operands &o = ops[i];
             if (launch_product(sp, o.a, o.a_neg, o.b, o.b_neg, o.c, o.c_neg, stream)) return IPM_ERR_CUDA;
         }
+        if ((plan->flags & IPM_VALIDATE) && launch_validate_batch(plan->vb, plan->d_ops, plan->err, stream))
+            return IPM_ERR_CUDA;
     }
     if (plan->flags & IPM_SYNC) return read_error(plan, stream);
     return IPM_OK;

@@ -177,6 +177,28 @@ uint64_t validation_point(uint64_t seed);
 int launch_validate(const ipm_plan_info &I, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                     const uint8_t *bn, const uint32_t *c, const uint8_t *cn, uint64_t t, uint64_t *part, int *err,
                     void *stream);
+// The same check for every product of a batched call, in two launches: one
+// warp per item (a chunk of up to VAL_ROWS rows of one operand of one
+// product, weighted by t^row0), then one thread per product.  Built once
+// by ipm_plan for the plan's fixed point t.
+constexpr int VAL_ROWS = 128;
+struct ValItem {
+    int32_t product, operand;  // operand 0: a, 1: b, 2: c
+    int64_t row0;
+    int32_t rows, limbs;
+    uint64_t t_row0;           // t^row0 mod 2^61 - 1
+};
+struct ValBatch {
+    const ValItem *items = nullptr;  // device
+    int64_t nitems = 0;
+    const int64_t *first = nullptr;  // device: first[3 i + o] = first item of product i, operand o; first[3 n] = nitems
+    int32_t nproducts = 0;
+    uint64_t *part = nullptr;        // device: one partial sum per item
+    uint64_t t = 0;
+};
+// Host: t^e mod 2^61 - 1 (the item weights).
+uint64_t pow61_host(uint64_t t, uint64_t e);
+int launch_validate_batch(const ValBatch &vb, const ipm_operands *ops, int *err, void *stream);
 // The same passes with every radix-16 stage on the tensor cores
 // (ipm_kernels_tc.cu); the launchers above call these when kp.tcfrag is set.
 int set_kernel_attributes_tc();

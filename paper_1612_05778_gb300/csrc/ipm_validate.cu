@@ -13,6 +13,8 @@
 // final block compares.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ipm_internal.h"
 
 namespace ipm {
@@ -100,6 +102,61 @@ __global__ void __launch_bounds__(VAL_THREADS) k_val_partial(const uint32_t *__r
     }
 }
 
+// Batched check, pass 1: one warp per item, Horner over its rows from the
+// top (acc = acc t + row value), then the weight t^row0.
+__global__ void __launch_bounds__(VAL_THREADS) k_valb_partial(const ValItem *__restrict__ items, int64_t nitems,
+                                                              const ipm_operands *__restrict__ ops, uint64_t t,
+                                                              uint64_t *__restrict__ part) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (VAL_THREADS / 32);
+    for (int64_t w = (int64_t)blockIdx.x * (VAL_THREADS / 32) + (threadIdx.x >> 5); w < nitems; w += warps) {
+        const ValItem it = items[w];
+        const ipm_operands &o = ops[it.product];
+        const uint32_t *x = it.operand == 0 ? o.a : it.operand == 1 ? o.b : o.c;
+        const uint8_t *xn = it.operand == 0 ? o.a_neg : it.operand == 1 ? o.b_neg : o.c_neg;
+        const int L = it.limbs;
+        const int e0 = (32 * lane) % 61;
+        uint64_t acc = 0;  // lane 0's
+        for (int j = it.rows - 1; j >= 0; --j) {
+            const int64_t i = it.row0 + j;
+            const uint32_t *r = x + i * L;
+            uint64_t v = 0;
+            int e = e0;
+            for (int l0 = lane; l0 < L; l0 += 8 * 32) {
+                uint64_t s8 = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int l = l0 + 32 * u;
+                    if (l < L) s8 += rot61(r[l], e);
+                    e += 48;
+                    if (e >= 61) e -= 61;
+                }
+                v = add61(v, red61(s8));
+            }
+            for (int off = 16; off; off >>= 1) v = add61(v, __shfl_down_sync(0xffffffffu, v, off));
+            if (lane == 0) {
+                if (xn[i] && v) v = Q61 - v;
+                acc = add61(mul61(acc, t), v);
+            }
+        }
+        if (lane == 0) part[w] = mul61(acc, it.t_row0);
+    }
+}
+
+// Batched check, pass 2: one thread per product sums its items.
+__global__ void k_valb_final(const int64_t *__restrict__ first, int32_t n, const uint64_t *__restrict__ part,
+                             int *err) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint64_t s[3];
+        for (int o = 0; o < 3; ++o) {
+            uint64_t acc = 0;
+            for (int64_t k = first[3 * i + o]; k < first[3 * i + o + 1]; ++k) acc = add61(acc, part[k]);
+            s[o] = acc;
+        }
+        if (mul61(s[0], s[1]) != s[2]) atomicOr(err, ERRBIT_MISMATCH);
+    }
+}
+
 // part: [3][VAL_BLOCKS] sums of a(t), b(t), c(t); sets ERRBIT_MISMATCH in
 // *err when a(t) b(t) != c(t) mod q.
 __global__ void __launch_bounds__(VAL_THREADS) k_val_final(const uint64_t *__restrict__ part, int *err) {
@@ -126,6 +183,26 @@ uint64_t splitmix64(uint64_t x) {
 }
 
 }  // namespace
+
+uint64_t pow61_host(uint64_t t, uint64_t e) {
+    uint64_t r = 1;
+    while (e) {
+        if (e & 1) r = red61((uint64_t)(((unsigned __int128)r * t) % Q61));
+        t = (uint64_t)(((unsigned __int128)t * t) % Q61);
+        e >>= 1;
+    }
+    return r;
+}
+
+int launch_validate_batch(const ValBatch &vb, const ipm_operands *ops, int *err, void *stream) {
+    if (vb.nitems == 0) return 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t blocks = std::min<int64_t>((vb.nitems + VAL_THREADS / 32 - 1) / (VAL_THREADS / 32), 152 * 64);
+    k_valb_partial<<<(unsigned)blocks, VAL_THREADS, 0, s>>>(vb.items, vb.nitems, ops, vb.t, vb.part);
+    k_valb_final<<<(vb.nproducts + 255) / 256, 256, 0, s>>>(vb.first, vb.nproducts, vb.part, err);
+    note_launches(2);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 uint64_t validation_point(uint64_t seed) {
     return 2 + red61(splitmix64(seed)) % (Q61 - 3);  // t in [2, q - 2]

@@ -93,3 +93,49 @@ def test_plan_flag_checks_every_product():
     plan.mul(da, dan, db, dbn)
     plan.sync()
     plan.close()
+
+
+def _batch(seed, count):
+    shapes = W.batch_shapes(seed=seed, count=count, dmin=16, dmax=900, bmin=32, bmax=700)
+    ops = W.batch_operands(shapes, seed=seed)
+    dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
+    return shapes, ops, dev
+
+
+@pytest.mark.parametrize("flags", [ipm.IPM_VALIDATE, ipm.IPM_VALIDATE | ipm.IPM_GRAPH])
+def test_batched_check_passes_exact_products(flags):
+    """Every product of a batched call checked in two launches, including
+    products that run alone (split middle transform, packed, schoolbook)."""
+    shapes, ops, dev = _batch(21, 14)
+    tuples = [(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes]
+    plan = ipm.Plan(tuples, flags=flags)
+    for _ in range(2):
+        outs = plan.mul_batched(dev)
+        plan.sync()
+    for (a, b), (c, cn), info in zip(ops, outs, plan.infos):
+        want = oracle.polymul(a, b, info["lc"])
+        got = ipm.to_host(c, cn)
+        assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    plan.close()
+
+
+def test_batched_check_catches_a_shared_output():
+    """Two products of one batched call handed the same output buffer (a
+    caller's mistake, made on the host): the buffer cannot hold both
+    products, and the check reports IPM_ERR_MISMATCH."""
+    rng = np.random.default_rng(31)
+    shape = (200, 150, 100, 90)
+    ops = [(W.random_poly(rng, 200, 100), W.random_poly(rng, 150, 90)) for _ in range(3)]
+    dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
+    plan = ipm.Plan([shape] * 3, flags=ipm.IPM_VALIDATE)
+    outs = [plan.empty_output(i) for i in range(3)]
+    outs[1] = outs[0]
+    plan.mul_batched(dev, outs)
+    with pytest.raises(ipm.IpmError) as e:
+        plan.sync()
+    assert e.value.status == 7
+    # separate buffers again: no alarm
+    outs = [plan.empty_output(i) for i in range(3)]
+    plan.mul_batched(dev, outs)
+    plan.sync()
+    plan.close()
