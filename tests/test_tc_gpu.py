@@ -78,6 +78,7 @@ CASES = [
     (129, 257, 95, 97, dict()),
     (1, 1, 1, 1, dict()),
     (5, 100, 31, 4096, dict()),
+    (20000, 20000, 16, 16, dict(kron=8)),         # Kronecker-packed operands, middle Y1 = 256
 ]
 
 
