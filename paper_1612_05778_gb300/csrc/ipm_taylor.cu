@@ -134,6 +134,98 @@ __global__ void k_taylor_add(const uint32_t *__restrict__ P, const uint8_t *__re
     }
 }
 
+// ---- the first levels in shared memory ----------------------------------------
+//
+// Levels 0..5 (blocks of up to TB = 64 coefficients) of every 64-block in
+// one kernel: a CUDA block holds its 64 coefficients as W-limb two's
+// complement values (W covers bits + 64 magnitude bits and the sign) and
+// runs the same recursion with additions only: at level b, T = the hi
+// blocks moved onto the lo positions, b steps T_k <- T_k + T_(k-1) inside
+// each 2b-window (a multiplication by x + 1 each), then A_k = T_k + lo_k.
+// One warp per coefficient row, ballot carry-lookahead over 32 limbs.
+constexpr int TB = 64;
+constexpr int TB_THREADS = 256;
+
+// dst = src + (b ? b : 0), W limbs, two's complement (mod 2^(32 W)).
+__device__ __forceinline__ void warp_add_rows(uint32_t *dst, const uint32_t *a, const uint32_t *b, int W) {
+    const int lane = threadIdx.x & 31;
+    unsigned cio = 0;
+    for (int q0 = 0; q0 < W; q0 += 32) {
+        const int q = q0 + lane;
+        const uint32_t x = q < W ? a[q] : 0u, y = (b && q < W) ? b[q] : 0u;
+        const uint32_t sum = x + y;
+        const unsigned cm = chain(__ballot_sync(0xffffffffu, sum < x), __ballot_sync(0xffffffffu, sum == 0xffffffffu),
+                                  &cio);
+        if (q < W) dst[q] = sum + ((cm >> lane) & 1u);
+    }
+}
+
+__global__ void __launch_bounds__(TB_THREADS) k_taylor_base(const uint32_t *__restrict__ f,
+                                                          const uint8_t *__restrict__ fn, int lf, int64_t n,
+                                                          uint32_t bits, int W, uint32_t *__restrict__ S,
+                                                          uint8_t *__restrict__ Sn, int LS, int *err) {
+    extern __shared__ uint32_t sm[];
+    uint32_t *A = sm, *T = sm + TB * W, *U = sm + 2 * TB * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = TB_THREADS / 32;
+    const int64_t base = (int64_t)blockIdx.x * TB;
+    // load: sign-magnitude -> two's complement (-x = ~x + 1)
+    for (int k = warp; k < TB; k += nw) {
+        const int64_t i = base + k;
+        const bool have = i < n;
+        const bool neg = have && fn[i] != 0;
+        unsigned cio = neg ? 1u : 0u;
+        for (int q0 = 0; q0 < W; q0 += 32) {
+            const int q = q0 + lane;
+            uint32_t x = (have && q < lf) ? f[i * lf + q] : 0u;
+            if (q == lf - 1 && (bits & 31u) && (x >> (bits & 31u))) atomicOr(err, ERRBIT_BOUND);
+            if (neg) x = ~x;
+            const unsigned cm = chain(0u, __ballot_sync(0xffffffffu, x == 0xffffffffu), &cio);
+            if (q < W) A[k * W + q] = x + ((cm >> lane) & 1u);
+        }
+    }
+    __syncthreads();
+    for (int b = 1; b < TB; b <<= 1) {
+        const int w2 = 2 * b;
+        for (int k = warp; k < TB; k += nw)  // T: hi moved down, zeros above
+            for (int q = lane; q < W; q += 32) T[k * W + q] = (k & (w2 - 1)) < b ? A[(k + b) * W + q] : 0u;
+        __syncthreads();
+        for (int step = 0; step < b; ++step) {  // T <- (x + 1) T inside each window
+            for (int k = warp; k < TB; k += nw) {
+                if ((k & (w2 - 1)) == 0)
+                    for (int q = lane; q < W; q += 32) U[k * W + q] = T[k * W + q];
+                else
+                    warp_add_rows(U + k * W, T + k * W, T + (k - 1) * W, W);
+            }
+            __syncthreads();
+            uint32_t *x = T;
+            T = U;
+            U = x;
+        }
+        for (int k = warp; k < TB; k += nw)  // A = T + lo
+            warp_add_rows(A + k * W, T + k * W, (k & (w2 - 1)) < b ? A + k * W : nullptr, W);
+        __syncthreads();
+    }
+    // store: two's complement -> sign-magnitude at stride LS
+    for (int k = warp; k < TB; k += nw) {
+        const int64_t i = base + k;
+        const bool neg = (A[k * W + W - 1] >> 31) != 0;
+        unsigned cio = neg ? 1u : 0u;
+        bool nonzero = false;
+        for (int q0 = 0; q0 < W; q0 += 32) {
+            const int q = q0 + lane;
+            uint32_t x = q < W ? A[k * W + q] : 0u;
+            if (neg) x = ~x;
+            const unsigned cm = chain(0u, __ballot_sync(0xffffffffu, x == 0xffffffffu), &cio);
+            const uint32_t r = x + ((cm >> lane) & 1u);
+            if (q < LS) S[i * LS + q] = r;
+            else if (q < W && r) atomicOr(err, ERRBIT_INTERNAL);
+            if (__ballot_sync(0xffffffffu, q < W && r != 0u)) nonzero = true;
+        }
+        for (int q = W + lane; q < LS; q += 32) S[i * LS + q] = 0u;
+        if (lane == 0) Sn[i] = (neg && nonzero) ? 1 : 0;
+    }
+}
+
 int grid_for(int64_t work, int per_block) {
     const int64_t b = (work + per_block - 1) / per_block;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
@@ -159,6 +251,12 @@ struct ipm_taylor_s {
     std::vector<int32_t> lq;         // lq[l]: stride of the level-l square
     std::vector<void *> mem;
     uint32_t *S[2] = {nullptr, nullptr}, *H = nullptr, *P = nullptr, *B = nullptr, *Q = nullptr;
+    // levels 0..5 in shared memory (k_taylor_base) when the plan has more
+    // levels and 3 TB W words fit a block; B64 = (x + 1)^64 (65 x 2 limbs)
+    bool base = false;
+    int base_w = 0;
+    uint32_t *B64 = nullptr;
+    uint8_t *B64n = nullptr;
     uint8_t *Sn[2] = {nullptr, nullptr}, *Hn = nullptr, *Pn = nullptr, *Bn = nullptr, *Qn = nullptr;
     int *err = nullptr;
 };
@@ -258,6 +356,32 @@ extern "C" ipm_status ipm_taylor_plan(ipm_taylor_t *out, int64_t deg, uint32_t b
         return st;
     }
     if (cudaMemset(t->err, 0, sizeof(int)) != cudaSuccess) { free_taylor(t); return IPM_ERR_CUDA; }
+    t->base_w = ceil_div32((int64_t)bits + TB + 1);
+    const size_t base_smem = (size_t)3 * TB * t->base_w * sizeof(uint32_t);
+    if (t->m > 6 && base_smem <= 200 * 1024) {
+        // C(64, k) < 2^63: two limbs per coefficient
+        std::vector<uint32_t> bin(2 * (TB + 1));
+        std::vector<uint8_t> binn(TB + 1, 0);
+        uint64_t c = 1;
+        for (int k = 0; k <= TB; ++k) {
+            bin[2 * k] = (uint32_t)c;
+            bin[2 * k + 1] = (uint32_t)(c >> 32);
+            // exact: C(64, k) (64 - k) = C(64, k+1) (k+1); the product needs 128 bits
+            c = (uint64_t)((unsigned __int128)c * (uint64_t)(TB - k) / (uint64_t)(k + 1));
+        }
+        if ((st = dalloc(t, &t->B64, bin.size())) || (st = dalloc(t, &t->B64n, binn.size()))) {
+            free_taylor(t);
+            return st;
+        }
+        if (cudaMemcpy(t->B64, bin.data(), bin.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(t->B64n, binn.data(), binn.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaFuncSetAttribute(k_taylor_base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base_smem) !=
+                cudaSuccess) {
+            free_taylor(t);
+            return IPM_ERR_CUDA;
+        }
+        t->base = true;
+    }
     *out = t;
     return IPM_OK;
 }
@@ -284,16 +408,29 @@ extern "C" ipm_status ipm_taylor_shift(ipm_taylor_t t, const uint32_t *f, const 
         if (!launched(2)) return IPM_ERR_CUDA;
         return (t->flags & IPM_SYNC) ? ipm_taylor_sync(t, stream) : IPM_OK;
     }
-    // level-0 state: f at its stride, rows n.. zero
-    int cur = 0;
-    k_taylor_rows<<<grid_for(n2 * t->ls[0], 256), 256, 0, s>>>(t->S[0], t->Sn[0], t->ls[0], f, f_neg, lf, t->n, n2,
-                                                               0, 0, t->bits, t->err);
-    k_taylor_xplus1<<<1, 64, 0, s>>>(t->B, t->Bn, 1);
-    if (!launched(2)) return IPM_ERR_CUDA;
-    for (int l = 0; l < t->m; ++l) {
+    int cur = 0, l0 = 0;
+    if (t->base) {
+        // levels 0..5 in shared memory: the level-6 state, and (x + 1)^64
+        const size_t smem = (size_t)3 * TB * t->base_w * sizeof(uint32_t);
+        k_taylor_base<<<(unsigned)(n2 / TB), TB_THREADS, smem, s>>>(f, f_neg, lf, t->n, t->bits, t->base_w, t->S[0],
+                                                                     t->Sn[0], t->ls[6], t->err);
+        if (cudaMemcpyAsync(t->B, t->B64, 2 * (TB + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(t->Bn, t->B64n, TB + 1, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return IPM_ERR_CUDA;
+        if (!launched(2)) return IPM_ERR_CUDA;
+        l0 = 6;
+    } else {
+        // level-0 state: f at its stride, rows n.. zero
+        k_taylor_rows<<<grid_for(n2 * t->ls[0], 256), 256, 0, s>>>(t->S[0], t->Sn[0], t->ls[0], f, f_neg, lf, t->n,
+                                                                   n2, 0, 0, t->bits, t->err);
+        k_taylor_xplus1<<<1, 64, 0, s>>>(t->B, t->Bn, 1);
+        if (!launched(2)) return IPM_ERR_CUDA;
+    }
+    for (int l = l0; l < t->m; ++l) {
         const int64_t b = 1ll << l;
         const int lbin = ceil_div32(b);
-        if (l >= 1) {  // (x+1)^b from (x+1)^(b/2), then back to the stride of its bound 2^b
+        if (l > l0) {  // (x+1)^b from (x+1)^(b/2), then back to the stride of its bound 2^b
             ipm_status st = ipm_mul(t->square[l], t->B, t->Bn, t->B, t->Bn, t->Q, t->Qn, stream);
             if (st != IPM_OK) return st;
             k_taylor_rows<<<grid_for((b + 1) * lbin, 256), 256, 0, s>>>(t->B, t->Bn, lbin, t->Q, t->Qn, t->lq[l],

@@ -45,8 +45,10 @@ def gpu_shift(f, bits, flags=0):
     return out, limbs
 
 
-@pytest.mark.parametrize("n,bits", [(1, 5), (2, 1), (3, 64), (8, 255), (100, 300), (257, 31), (513, 1000),
-                                    (1024, 255)])
+# n <= 64 runs every level through products; n > 64 runs levels 0..5 in
+# shared memory first, unless the coefficients are too wide for it (9000 bits)
+@pytest.mark.parametrize("n,bits", [(1, 5), (2, 1), (3, 64), (8, 255), (64, 100), (65, 100), (100, 300), (257, 31),
+                                    (513, 1000), (1024, 255), (200, 9000)])
 def test_taylor_matches_oracle(n, bits):
     rng = np.random.default_rng(n * 13 + bits)
     f = W.random_poly(rng, n, bits)
@@ -87,11 +89,12 @@ def test_taylor_negative_zero_and_sparse():
     assert all(gn[k] == 0 for k in range(len(vals)) if want[k] == 0)
 
 
-def test_taylor_bound_violation_reported():
+@pytest.mark.parametrize("n", [64, 300])
+def test_taylor_bound_violation_reported(n):
     rng = np.random.default_rng(8)
-    f = W.random_poly(rng, 64, 40)
+    f = W.random_poly(rng, n, 40)
     f[0][10, 1] |= 1 << 12  # bit 44 set, above the 40-bit bound
-    ts = ipm.TaylorShift(64, 40)
+    ts = ipm.TaylorShift(n, 40)
     df, dfn = ipm.to_device(*f)
     ts.shift(df, dfn)
     with pytest.raises(ipm.IpmError) as e:
