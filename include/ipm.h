@@ -358,8 +358,11 @@ ipm_status ipm_sync(ipm_plan_t plan, ipm_stream_t stream);
  * f padded to n' = 2^m coefficients; at level l (blocks of b = 2^l,
  * already shifted) every pair of blocks (lo, hi) becomes lo + (x+1)^b hi,
  * all pairs of a level in ONE ipm_mul of (x+1)^b by the hi blocks placed
- * 2b apart; (x+1)^b is the square of (x+1)^(b/2) (ipm_mul); the block
- * additions are sign-magnitude additions on the GPU.
+ * 2b apart; (x+1)^b is the square of (x+1)^(b/2) (ipm_mul), all of them
+ * computed once by ipm_taylor_plan (which therefore runs work on the GPU
+ * and waits for it); the first six levels run in shared memory with
+ * additions only; the block additions are sign-magnitude additions on the
+ * GPU.
  *
  * Layout: f and g as in ipm_mul (device pointers, sign-magnitude 32-bit
  * limbs); f has stride ceil(bits/32), g has deg+1 coefficients with stride

@@ -14,7 +14,8 @@
 // product: with H(x) = sum_j hi_j(x) x^(2bj) (the hi blocks moved onto the
 // lo positions, zeros in between), (x + 1)^b H(x) holds every
 // (x + 1)^b hi_j, of degree 2b - 1, in its own block [2bj, 2bj + 2b).
-// The binomial polynomial (x + 1)^b is the square of (x + 1)^(b/2).
+// The binomial polynomial (x + 1)^b is the square of (x + 1)^(b/2); the
+// plan computes all of them once (they do not depend on f).
 //
 // Bounds: a shifted block of B coefficients below 2^bits in magnitude has
 // |coefficient k| <= (2^bits - 1) C(B, k + 1) < 2^(bits + B), and
@@ -244,20 +245,22 @@ struct ipm_taylor_s {
     int m = 0;              // levels
     uint32_t flags = 0;
     int32_t lg = 0;         // output limb stride
-    std::vector<ipm_plan_t> square;  // square[l]: (x+1)^(2^(l-1)) squared (l >= 1)
+    std::vector<ipm_plan_t> square;  // square[l]: (x+1)^(2^(l-1)) squared (l >= 1); plan time only
     std::vector<ipm_plan_t> level;   // level[l]: (x+1)^b times H
     std::vector<int32_t> ls;         // ls[l]: stride of the level-l state (bound bits + 2^l)
     std::vector<int32_t> lp;         // lp[l]: stride of the level-l product
     std::vector<int32_t> lq;         // lq[l]: stride of the level-l square
     std::vector<void *> mem;
-    uint32_t *S[2] = {nullptr, nullptr}, *H = nullptr, *P = nullptr, *B = nullptr, *Q = nullptr;
+    uint32_t *S[2] = {nullptr, nullptr}, *H = nullptr, *P = nullptr, *Q = nullptr;
+    uint8_t *Sn[2] = {nullptr, nullptr}, *Hn = nullptr, *Pn = nullptr, *Qn = nullptr;
     // levels 0..5 in shared memory (k_taylor_base) when the plan has more
-    // levels and 3 TB W words fit a block; B64 = (x + 1)^64 (65 x 2 limbs)
+    // levels and 3 TB W words fit a block
     bool base = false;
     int base_w = 0;
-    uint32_t *B64 = nullptr;
-    uint8_t *B64n = nullptr;
-    uint8_t *Sn[2] = {nullptr, nullptr}, *Hn = nullptr, *Pn = nullptr, *Bn = nullptr, *Qn = nullptr;
+    // (x + 1)^(2^l) of every level l, computed once by the plan (they do not
+    // depend on f): b + 1 coefficients at stride ceil(b / 32), 16-byte aligned
+    std::vector<uint32_t *> Bl;
+    std::vector<uint8_t *> Bln;
     int *err = nullptr;
 };
 
@@ -343,13 +346,11 @@ extern "C" ipm_status ipm_taylor_plan(ipm_taylor_t *out, int64_t deg, uint32_t b
         t->lp.push_back(I.lc);
         lpmax = std::max(lpmax, I.lc);
     }
-    const int32_t lb = std::max(1, ceil_div32(t->n2 / 2));
     const size_t n2 = (size_t)t->n2;
     if ((st = dalloc(t, &t->S[0], n2 * lsmax)) || (st = dalloc(t, &t->S[1], n2 * lsmax)) ||
         (st = dalloc(t, &t->Sn[0], n2)) || (st = dalloc(t, &t->Sn[1], n2)) ||
         (st = dalloc(t, &t->H, n2 * lsmax)) || (st = dalloc(t, &t->Hn, n2)) ||
         (st = dalloc(t, &t->P, n2 * lpmax)) || (st = dalloc(t, &t->Pn, n2)) ||
-        (st = dalloc(t, &t->B, (n2 / 2 + 1) * lb + 2)) || (st = dalloc(t, &t->Bn, n2 / 2 + 2)) ||
         (st = dalloc(t, &t->Q, (n2 / 2 + 1) * lqmax)) || (st = dalloc(t, &t->Qn, n2 / 2 + 2)) ||
         (st = dalloc(t, &t->err, 4))) {
         free_taylor(t);
@@ -359,28 +360,62 @@ extern "C" ipm_status ipm_taylor_plan(ipm_taylor_t *out, int64_t deg, uint32_t b
     t->base_w = ceil_div32((int64_t)bits + TB + 1);
     const size_t base_smem = (size_t)3 * TB * t->base_w * sizeof(uint32_t);
     if (t->m > 6 && base_smem <= 200 * 1024) {
-        // C(64, k) < 2^63: two limbs per coefficient
-        std::vector<uint32_t> bin(2 * (TB + 1));
-        std::vector<uint8_t> binn(TB + 1, 0);
-        uint64_t c = 1;
-        for (int k = 0; k <= TB; ++k) {
-            bin[2 * k] = (uint32_t)c;
-            bin[2 * k + 1] = (uint32_t)(c >> 32);
-            // exact: C(64, k) (64 - k) = C(64, k+1) (k+1); the product needs 128 bits
-            c = (uint64_t)((unsigned __int128)c * (uint64_t)(TB - k) / (uint64_t)(k + 1));
-        }
-        if ((st = dalloc(t, &t->B64, bin.size())) || (st = dalloc(t, &t->B64n, binn.size()))) {
-            free_taylor(t);
-            return st;
-        }
-        if (cudaMemcpy(t->B64, bin.data(), bin.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(t->B64n, binn.data(), binn.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaFuncSetAttribute(k_taylor_base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base_smem) !=
-                cudaSuccess) {
+        if (cudaFuncSetAttribute(k_taylor_base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base_smem) !=
+            cudaSuccess) {
             free_taylor(t);
             return IPM_ERR_CUDA;
         }
         t->base = true;
+    }
+    // the binomial polynomials, once: (x + 1), then squarings (the square
+    // plans are not needed afterwards and are freed)
+    if (t->m > 0) {
+        size_t words = 0;
+        for (int l = 0; l < t->m; ++l) {
+            const int64_t b = 1ll << l;
+            words += ((size_t)(b + 1) * ceil_div32(b) + 3) & ~(size_t)3;
+        }
+        uint32_t *arena = nullptr;
+        uint8_t *arena_n = nullptr;
+        if ((st = dalloc(t, &arena, words)) || (st = dalloc(t, &arena_n, (size_t)t->n2 + t->m))) {
+            free_taylor(t);
+            return st;
+        }
+        size_t off = 0, off_n = 0;
+        for (int l = 0; l < t->m; ++l) {
+            const int64_t b = 1ll << l;
+            t->Bl.push_back(arena + off);
+            t->Bln.push_back(arena_n + off_n);
+            off += ((size_t)(b + 1) * ceil_div32(b) + 3) & ~(size_t)3;
+            off_n += (size_t)b + 1;
+        }
+        k_taylor_xplus1<<<1, 64>>>(t->Bl[0], t->Bln[0], 1);
+        note_launches(1);
+        for (int l = 1; l < t->m; ++l) {
+            const int64_t b = 1ll << l;
+            const int lbin = ceil_div32(b);
+            if ((st = ipm_mul(t->square[l], t->Bl[l - 1], t->Bln[l - 1], t->Bl[l - 1], t->Bln[l - 1], t->Q, t->Qn,
+                              nullptr)) != IPM_OK) {
+                free_taylor(t);
+                return st;
+            }
+            k_taylor_rows<<<grid_for((b + 1) * lbin, 256), 256>>>(t->Bl[l], t->Bln[l], lbin, t->Q, t->Qn, t->lq[l],
+                                                                  b + 1, b + 1, 0, 0, 0u, t->err);
+            note_launches(1);
+        }
+        if (cudaStreamSynchronize(nullptr) != cudaSuccess) { free_taylor(t); return IPM_ERR_CUDA; }
+        for (auto &p : t->square)
+            if (p) {
+                const ipm_status sst = ipm_sync(p, nullptr);
+                ipm_destroy(p);
+                p = nullptr;
+                if (sst != IPM_OK) { free_taylor(t); return sst; }
+            }
+        int h = 0;
+        if (cudaMemcpy(&h, t->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || h) {
+            free_taylor(t);
+            return IPM_ERR_CUDA;
+        }
     }
     *out = t;
     return IPM_OK;
@@ -414,35 +449,22 @@ extern "C" ipm_status ipm_taylor_shift(ipm_taylor_t t, const uint32_t *f, const 
         const size_t smem = (size_t)3 * TB * t->base_w * sizeof(uint32_t);
         k_taylor_base<<<(unsigned)(n2 / TB), TB_THREADS, smem, s>>>(f, f_neg, lf, t->n, t->bits, t->base_w, t->S[0],
                                                                      t->Sn[0], t->ls[6], t->err);
-        if (cudaMemcpyAsync(t->B, t->B64, 2 * (TB + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(t->Bn, t->B64n, TB + 1, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return IPM_ERR_CUDA;
-        if (!launched(2)) return IPM_ERR_CUDA;
+        if (!launched(1)) return IPM_ERR_CUDA;
         l0 = 6;
     } else {
         // level-0 state: f at its stride, rows n.. zero
         k_taylor_rows<<<grid_for(n2 * t->ls[0], 256), 256, 0, s>>>(t->S[0], t->Sn[0], t->ls[0], f, f_neg, lf, t->n,
                                                                    n2, 0, 0, t->bits, t->err);
-        k_taylor_xplus1<<<1, 64, 0, s>>>(t->B, t->Bn, 1);
-        if (!launched(2)) return IPM_ERR_CUDA;
+        if (!launched(1)) return IPM_ERR_CUDA;
     }
     for (int l = l0; l < t->m; ++l) {
         const int64_t b = 1ll << l;
-        const int lbin = ceil_div32(b);
-        if (l > l0) {  // (x+1)^b from (x+1)^(b/2), then back to the stride of its bound 2^b
-            ipm_status st = ipm_mul(t->square[l], t->B, t->Bn, t->B, t->Bn, t->Q, t->Qn, stream);
-            if (st != IPM_OK) return st;
-            k_taylor_rows<<<grid_for((b + 1) * lbin, 256), 256, 0, s>>>(t->B, t->Bn, lbin, t->Q, t->Qn, t->lq[l],
-                                                                        b + 1, b + 1, 0, 0, 0u, t->err);
-            if (!launched(1)) return IPM_ERR_CUDA;
-        }
         // H: the hi blocks moved onto the lo positions
         const int L = t->ls[l];
         k_taylor_rows<<<grid_for((n2 - b) * L, 256), 256, 0, s>>>(t->H, t->Hn, L, t->S[cur], t->Sn[cur], L, n2,
                                                                   n2 - b, b, b, 0u, t->err);
         if (!launched(1)) return IPM_ERR_CUDA;
-        ipm_status st = ipm_mul(t->level[l], t->B, t->Bn, t->H, t->Hn, t->P, t->Pn, stream);
+        ipm_status st = ipm_mul(t->level[l], t->Bl[l], t->Bln[l], t->H, t->Hn, t->P, t->Pn, stream);
         if (st != IPM_OK) return st;
         // the new state: the product plus the lo blocks
         const bool last = l + 1 == t->m;
