@@ -488,7 +488,10 @@ def run_taylor(args):
     ipm_build.build()
     import paper_1612_05778_gb300 as ipm
     (n, bits), f = W.taylor_dense(seed=5)
-    ts = ipm.TaylorShift(n, bits)
+    # the level products take the plans the learned dispatch picks
+    from paper_1612_05778_gb300 import costmodel as cmod
+    cmod.install(points=cmod.load_sweep()["points"])
+    ts = ipm.TaylorShift(n, bits, flags=ipm.IPM_COSTMODEL)
     df, dfn = ipm.to_device(*f)
     g = torch.empty((n, ts.limbs), dtype=torch.int32, device="cuda")
     gn = torch.empty((n,), dtype=torch.uint8, device="cuda")
@@ -535,6 +538,7 @@ def run_taylor(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "taylor: n=16384 coefficients, |f_i| < 2^4096, signed uniform, seed 5",
+                       "dispatch": "IPM_COSTMODEL (learned plan per level product)",
                        "output_limbs": ts.limbs, "levels": int(math.log2(n)),
                        "l2": "flushed between timed steps (512 MiB write, outside the events)"},
             "cpu_baseline": cpu, "gpu_launches": int(launches), "launches_per_step": launches / args.steps,
