@@ -1,5 +1,5 @@
 """Learned plan dispatch: train the cost model on autotuning sweep records
-and judge it by its regret against the exhaustive sweep.
+and measure it by its regret against the exhaustive sweep.
 
 The paper picks its split (DetermineBase, §2.4) by table look-up; here every
 candidate plan of a shape (``candidates``: each valid digit split K with the
