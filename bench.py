@@ -893,6 +893,11 @@ def main(argv=None):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("batch", "taylor", "paper_table"):
+        # one-GPU measurements: under torchrun only rank 0 runs them
+        world, rank, _ = dist_env()
+        if world > 1 and rank != 0:
+            return 0
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "taylor":

@@ -47,3 +47,11 @@ def test_algorithmic_bytes_match_measured_reads(large_dense_info):
 def test_stage_bits(logL, want):
     assert bench.stage_bits(logL) == want
     assert sum(want) == logL
+
+
+@pytest.mark.parametrize("workload", ["batch", "taylor", "paper_table"])
+def test_single_gpu_workloads_leave_other_ranks_idle(workload, monkeypatch):
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    assert bench.main(["--workload", workload, "--gpus", "2"]) == 0
