@@ -65,6 +65,7 @@ UNIT = "products/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 PASS_NAMES = ["k_forward", "k_middle", "k_inverse"]
+E2E_INFLIGHT = 3  # products in flight in the end-to-end measurement
 KERNEL_SRC = [os.path.join(ROOT, "paper_1612_05778_gb300", "csrc", n)
               for n in ("ipm_kernels.cu", "passes.cuh", "ntt_stages.cuh", "modarith.cuh", "ipm_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_large_dense.md")
@@ -797,39 +798,42 @@ def run_ours(args):
 
     # end to end through the host-buffer ABI (pinned host memory): every step
     # copies its inputs in, multiplies and copies its result out, all inside
-    # the timed region; two plans on two streams keep two products in flight
-    # so one product's copies overlap the other's compute (ipm_mul_host_async)
+    # the timed region; E2E_INFLIGHT plans on as many streams keep that many
+    # products in flight so their copies overlap the others' compute
+    # (ipm_mul_host_async; measured on a GB300: 699 products/s with two,
+    # 765 with three, 765 with four)
     e2e = None
     if not args.no_e2e:
         pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()  # noqa: E731
         ha, han, hb, hbn = pin(a[0]), pin(a[1]), pin(b[0]), pin(b[1])
-        plans = [ipm.Plan(shape, flags=flags) for _ in range(2)]
-        streams = [torch.cuda.Stream() for _ in range(2)]
+        nf = E2E_INFLIGHT
+        plans = [ipm.Plan(shape, flags=flags) for _ in range(nf)]
+        streams = [torch.cuda.Stream() for _ in range(nf)]
         outs = [(torch.empty((info["nc"], info["lc"]), dtype=torch.int32).pin_memory().numpy().view(np.uint32),
-                 torch.empty((info["nc"],), dtype=torch.uint8).pin_memory().numpy()) for _ in range(2)]
+                 torch.empty((info["nc"],), dtype=torch.uint8).pin_memory().numpy()) for _ in range(nf)]
 
         def e2e_steps(k):
             for i in range(k):
-                hc, hcn = outs[i % 2]
-                plans[i % 2].mul_host_async(ha, han, hb, hbn, hc, hcn, stream=streams[i % 2])
+                hc, hcn = outs[i % nf]
+                plans[i % nf].mul_host_async(ha, han, hb, hbn, hc, hcn, stream=streams[i % nf])
             for pl, st in zip(plans, streams):
                 pl.sync(st)
 
-        e2e_steps(4)
-        n_e2e = max(4, args.steps)
+        e2e_steps(2 * nf)
+        n_e2e = max(4 * nf, 2 * args.steps)
         barrier(dist)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2e_steps(n_e2e)
         dt = max_over_ranks(dist, time.perf_counter() - t0, dev)
-        if not (np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])):
+        if not all(np.array_equal(outs[0][0], o[0]) and np.array_equal(outs[0][1], o[1]) for o in outs[1:]):
             raise SystemExit("end-to-end products disagree")
         h2d = ha.nbytes + han.nbytes + hb.nbytes + hbn.nbytes
         d2h = outs[0][0].nbytes + outs[0][1].nbytes
         e2e = {"value": world * n_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
-               "api": "ipm_mul_host_async on two plans and two streams (pinned host buffers; copies in, "
-                      "product, copies out), then ipm_sync; host wall clock"}
+               "api": "ipm_mul_host_async on %d plans and %d streams (pinned host buffers; copies in, "
+                      "product, copies out), then ipm_sync; host wall clock" % (nf, nf)}
         for pl in plans:
             pl.close()
 
