@@ -267,8 +267,10 @@ ipm_status ipm_mul_host(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg
  * The host buffers must stay valid until then and should be pinned (copies
  * from pageable memory are not asynchronous).  Calls on one plan share its
  * device buffers, so they must be ordered on one stream; a caller overlaps
- * the copies of one product with the compute of another by using two plans
- * on two streams.
+ * the copies of some products with the compute of others by using several
+ * plans on as many streams (three products in flight reach 99% of the
+ * device-resident rate for two degree-32767 polynomials of 4096 bits on a
+ * GB300; two reach 90%).
  */
 ipm_status ipm_mul_host_async(ipm_plan_t plan, const uint32_t *a, const uint8_t *a_neg,
                               const uint32_t *b, const uint8_t *b_neg,
