@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ipm_internal.h"
+#include "ipm_mid256.h"
 
 using namespace ipm;
 
@@ -24,6 +25,7 @@ struct ipm_plan_s {
     size_t io_bytes = 0;
     // batched calls (n > 1): groups of products launched together
     std::vector<BatchLaunch> batch;
+    std::vector<char> batch_mid256;   // per group: middle pass in 256-thread blocks, two per SM
     ipm_operands *d_ops = nullptr;    // operand pointers of the current call
     // IPM_GRAPH: the grouped launches captured once into a CUDA graph
     cudaStream_t capture_stream = nullptr;
@@ -177,6 +179,19 @@ size_t batch_workspace_words(const std::vector<ShapePlan> &shapes) {
 // operand pointers from the plan's device table (d_ops), which each call
 // refreshes before launching the graph, so the graph stays valid for any
 // operands.  Products that run alone are launched outside the graph.
+// One group's three passes: the middle one in 256-thread blocks when the
+// group qualifies (batch_mid256), else all three by launch_batch.
+int launch_group(ipm_plan_s *plan, size_t g, void *stream) {
+    const BatchLaunch &bl = plan->batch[g];
+    if (!plan->batch_mid256[g]) return launch_batch(bl, plan->d_ops, stream);
+    BatchLaunch fwd = bl, inv = bl;
+    fwd.items[1] = fwd.items[2] = nullptr;
+    inv.items[0] = inv.items[1] = nullptr;
+    if (launch_batch(fwd, plan->d_ops, stream)) return -1;
+    if (launch_batch_middle256(bl, stream)) return -1;
+    return launch_batch(inv, plan->d_ops, stream);
+}
+
 ipm_status capture_batch(ipm_plan_s *plan) {
     cudaError_t ce;
     if (!plan->capture_stream) {
@@ -187,8 +202,8 @@ ipm_status capture_batch(ipm_plan_s *plan) {
     ce = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (ce != cudaSuccess) return cuda_status(ce);
     bool failed = false;
-    for (const auto &bl : plan->batch)
-        if (launch_batch(bl, plan->d_ops, plan->capture_stream)) failed = true;
+    for (size_t g = 0; g < plan->batch.size(); ++g)
+        if (launch_group(plan, g, plan->capture_stream)) failed = true;
     cudaGraph_t g = nullptr;
     ce = cudaStreamEndCapture(plan->capture_stream, &g);
     const int captured = (int)(launches_so_far() - before);
@@ -308,6 +323,9 @@ ipm_status build_batch(ipm_plan_s *plan) {
             bl.nitems[p] = (unsigned)items[p].size();
         }
         plan->batch.push_back(bl);
+        bool m256 = true;
+        for (int i : g) m256 = m256 && mid256_ok(shapes[(size_t)i].kp, bl.smem[1]);
+        plan->batch_mid256.push_back(m256 ? 1 : 0);
     }
     return IPM_OK;
 }
@@ -326,7 +344,7 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
     plan->flags = flags;
     cudaError_t ce = cudaGetDevice(&plan->device);
     if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
-    if (set_kernel_attributes()) { free_plan(plan); return IPM_ERR_CUDA; }
+    if (set_kernel_attributes() || set_kernel_attributes_mid256()) { free_plan(plan); return IPM_ERR_CUDA; }
     plan->shapes.resize((size_t)n);
     size_t zmax = 0;
     std::vector<ipm_params> learned;
@@ -518,8 +536,8 @@ ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n, 
             if (ce != cudaSuccess) return cuda_status(ce);
             note_launches(plan->graph_kernels);
         } else {
-            for (const auto &bl : plan->batch)
-                if (launch_batch(bl, plan->d_ops, stream)) return IPM_ERR_CUDA;
+            for (size_t g = 0; g < plan->batch.size(); ++g)
+                if (launch_group(plan, g, stream)) return IPM_ERR_CUDA;
         }
         // products whose middle transform is split or whose operands are
         // packed run one after another

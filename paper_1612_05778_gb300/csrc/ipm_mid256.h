@@ -1,0 +1,17 @@
+// ipm_mid256.h -- the 256-thread middle pass of batched launches
+// (ipm_kernels_mid256.cu).
+#pragma once
+#include <stddef.h>
+
+#include "ipm_internal.h"
+
+namespace ipm {
+
+// Largest middle tile for which two 256-thread blocks share an SM.
+constexpr size_t MID256_SMEM_MAX = 113 * 1024;
+
+int set_kernel_attributes_mid256();
+int launch_batch_middle256(const BatchLaunch &bl, void *stream);
+bool mid256_ok(const KParams &kp, size_t smem_mid);
+
+}  // namespace ipm
