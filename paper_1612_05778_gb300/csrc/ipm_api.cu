@@ -124,15 +124,19 @@ ipm_status read_error(ipm_plan_s *plan, void *stream) {
 constexpr size_t kBatchWorkspaceWords = (size_t)1 << 30;
 
 struct VariantKey {
-    bool fwd_small, mid_tables, inv_small;
+    bool fwd_small, mid_tables, inv_small, mid256;
     bool operator<(const VariantKey &o) const {
-        return std::tie(fwd_small, mid_tables, inv_small) < std::tie(o.fwd_small, o.mid_tables, o.inv_small);
+        return std::tie(fwd_small, mid_tables, inv_small, mid256) <
+               std::tie(o.fwd_small, o.mid_tables, o.inv_small, o.mid256);
     }
 };
 
+// mid256: the product's middle tiles can run as 256-thread blocks, two per
+// SM (ipm_kernels_mid256.cu); such products are grouped apart so that one
+// large tile does not keep a whole group on the 512-thread blocks
 VariantKey variant_of(const ShapePlan &sp) {
     return VariantKey{sp.smem_fwd <= SMEM_FWD_3PERSM, sp.kp.mid_tables_in_smem != 0,
-                      sp.smem_inv <= SMEM_INV_2PERSM};
+                      sp.smem_inv <= SMEM_INV_2PERSM, mid256_ok(sp.kp, sp.smem_mid)};
 }
 
 // Groups of shape indices: same kernel variants, bounded workspace,
