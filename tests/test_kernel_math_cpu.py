@@ -1,0 +1,92 @@
+"""The arithmetic identities two GPU kernels rely on, restated with Python
+integers and checked exhaustively or on random values -- so the reasoning
+behind them is pinned on the CPU (the kernels themselves are compared with
+the oracle by the GPU tests).
+
+Randomised product check (csrc/ipm_validate.cu), q = 2^61 - 1:
+* a limb x < 2^32 times 2^e (e < 61) modulo q is the rotation
+  ((x << e) mod 2^64 & q) | (x >> (61 - e)) of the 64-bit kernel code;
+* 2^(32 l) mod q = 2^(32 l mod 61), and 32 (l + 32) = 32 l + 48 mod 61, the
+  lane stride of the limb loop;
+* eight rotated limbs (each < 2^61) sum below 2^64, so one reduction per
+  eight suffices.
+
+Tensor-core radix-16 stage (ntt_stages.cuh, stage_tc16), for a prime p:
+* with x_k = sum_s x_k^(s) 2^(8s) (bytes) and C[j][k][s] = E[j][k] 2^(8s)
+  2^32 mod p split into bytes C^(l), V_j = sum_l 2^(8l) D_l[j] with
+  D_l[j] = sum_{k,s} C^(l)[j][k][s] x_k^(s) is congruent to 2^32 sum_k
+  E[j][k] x_k, every D_l < 2^22 and V < 2^46 < p 2^32; Montgomery's REDC of
+  V gives the DFT output in [0, 2p).
+"""
+import numpy as np
+import pytest
+
+Q = (1 << 61) - 1
+MASK64 = (1 << 64) - 1
+
+
+def rot61(x, e):
+    if e == 0:
+        return x
+    return (((x << e) & MASK64) & Q) | (x >> (61 - e))
+
+
+def test_rotation_is_multiplication_by_a_power_of_two():
+    rng = np.random.default_rng(1)
+    xs = [0, 1, 0xFFFFFFFF, 0x80000000] + [int(v) for v in rng.integers(0, 2**32, 200)]
+    for e in range(61):
+        for x in xs:
+            assert rot61(x, e) == (x << e) % Q
+
+
+def test_limb_weights_and_lane_stride():
+    for lane in range(32):
+        e = (32 * lane) % 61
+        for k in range(20):
+            l = lane + 32 * k
+            assert pow(2, 32 * l, Q) == pow(2, e, Q) == 1 << e
+            e = (e + 48) % 61
+
+
+def test_eight_rotated_limbs_fit_64_bits():
+    assert 8 * (Q - 1) < 1 << 64  # rot61 of a value below 2^61 stays below 2^61
+    assert all(rot61(0xFFFFFFFF, e) < 1 << 61 for e in range(61))
+
+
+def brev4(j):
+    return int(format(j, "04b")[::-1], 2)
+
+
+@pytest.mark.parametrize("p", [1012924417, 1004535809, 998244353])
+@pytest.mark.parametrize("forward", [True, False])
+def test_byte_slice_dft_identity(p, forward):
+    # a primitive 16th root (any; the identity does not depend on which)
+    w = None
+    for cand in range(2, 200):
+        r = pow(cand, (p - 1) // 16, p)
+        if pow(r, 8, p) != 1:
+            w = r
+            break
+    assert w is not None and pow(w, 16, p) == 1
+    wi = pow(w, p - 2, p)
+    E = [[pow(w, (brev4(j) * k) % 16, p) if forward else pow(wi, (j * brev4(k)) % 16, p) for k in range(16)]
+         for j in range(16)]
+    C = [[[E[j][k] * pow(2, 8 * s + 32, p) % p for s in range(4)] for k in range(16)] for j in range(16)]
+    mont = (-pow(p, -1, 1 << 32)) % (1 << 32)
+    rng = np.random.default_rng(p % 1000 + forward)
+    for trial in range(20):
+        x = [int(v) for v in rng.integers(0, 2**32, 16)]  # any 32-bit words
+        if trial == 0:
+            x = [0xFFFFFFFF] * 16  # the largest bytes
+        for j in range(16):
+            D = [sum(((C[j][k][s] >> (8 * l)) & 255) * ((x[k] >> (8 * s)) & 255) for k in range(16) for s in range(4))
+                 for l in range(4)]
+            assert all(d <= 64 * 255 * 255 < 1 << 22 for d in D)
+            V = sum(d << (8 * l) for l, d in enumerate(D))
+            assert V < 1 << 46 < p << 32
+            assert V % p == (sum(E[j][k] * x[k] for k in range(16)) << 32) % p
+            # REDC: (V + m p) / 2^32 with m = (V mod 2^32) (-p^-1) mod 2^32
+            m = ((V & 0xFFFFFFFF) * mont) & 0xFFFFFFFF
+            r = (V + m * p) >> 32
+            assert (V + m * p) % (1 << 32) == 0 and r < 2 * p
+            assert r % p == sum(E[j][k] * x[k] for k in range(16)) % p
