@@ -306,29 +306,33 @@ ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n,
 /*
  * A product that allocates nothing (no counterpart in the paper; this is an
  * interface convenience).  For callers that cannot allocate device memory
- * while they run: code recording a CUDA graph by stream capture (cudaMalloc
- * is not permitted during capture), real-time services that forbid
- * allocator calls (cudaMalloc may synchronise the device), and plugins
- * whose host application owns all memory and hands over only the operand
- * buffers.
+ * while they run: services with latency limits that forbid allocator calls
+ * (cudaMalloc may synchronise the device and take milliseconds), and
+ * plugins whose host application owns all memory and hands over only the
+ * operand and output buffers.
  *
  * Same arguments and layouts as ipm_mul (device pointers), but no plan: the
- * shape is given directly and the planner's default choices are used.  The
- * product's scratch -- error word, twiddle tables and transform workspace --
- * lives in one static device array of IPM_NOALLOC_SCRATCH_BYTES that every
- * GPU loading this library holds until the process exits; products whose
- * scratch does not fit return IPM_ERR_UNSUPPORTED (for example two
- * degree-1023 polynomials with 255-bit coefficients need 0.85 MiB, two of
- * degree 2047 with 2048-bit coefficients 12.2 MiB, two of degree 4095 with
- * 4096-bit coefficients 48.4 MiB, which is rejected).
+ * shape is given directly and the planner's default choices are used.  c
+ * must hold (deg_a + deg_b + 1) rows of
+ *     Lc = ceil((bits_a + bits_b + ceil(log2 min(deg_a + 1, deg_b + 1))) / 32)
+ * limbs (the stride ipm_plan_info.lc reports); the library cannot check the
+ * size of a raw pointer's buffer, and a smaller c is written past its end.
+ * The product's scratch -- error word, twiddle tables and transform
+ * workspace -- lives in one static device array of IPM_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading this library holds until the process exits;
+ * products whose scratch does not fit return IPM_ERR_UNSUPPORTED (for
+ * example two degree-1023 polynomials with 255-bit coefficients need 0.85
+ * MiB, two of degree 2047 with 2048-bit coefficients 12.2 MiB, two of
+ * degree 4095 with 4096-bit coefficients 48.4 MiB, which is rejected).
  *
  * The first call on a device looks up the array's device address and sets
  * kernel limits: make it before any stream capture.  All calls share the
  * array, which keeps the previous call's contents (the error word is
- * cleared and the tables rewritten each call), so calls that overlap on the
- * GPU -- from several streams or host threads -- race: issue them one after
- * another.  The call waits for `stream` and returns the product's status
- * (IPM_ERR_BOUND for an input above its bit bound).
+ * cleared and the tables rewritten each call).  Calls are serialised by a
+ * host lock and each one waits for its `stream` before it returns, so two
+ * calls never overlap on the GPU; what can still race is the caller's own
+ * work on other streams that touches c while a call runs.  Returns the
+ * product's status (IPM_ERR_BOUND for an input above its bit bound).
  */
 #define IPM_NOALLOC_SCRATCH_BYTES (32u << 20)
 ipm_status ipm_mul_noalloc(const ipm_shape *shape, const uint32_t *a, const uint8_t *a_neg,
@@ -339,9 +343,12 @@ ipm_status ipm_mul_noalloc(const ipm_shape *shape, const uint32_t *a, const uint
  * Randomised check of a finished product (no counterpart in the paper):
  * evaluates a, b and c at one point t derived from `seed` modulo the
  * Mersenne prime q = 2^61 - 1 on the GPU and compares c(t) with a(t) b(t).
- * A c that differs from the exact product a*b in any limb or sign passes
- * with probability at most deg(c) / q < 2^-40 (Schwartz-Zippel); the exact
- * product always passes.  Layouts as in ipm_mul for `shape` (device
+ * The exact product always passes.  A wrong c is caught with probability at
+ * least 1 - deg(c) / q > 1 - 2^-40 whenever the error polynomial c - a*b is
+ * non-zero modulo q (Schwartz-Zippel: a non-zero polynomial of degree D
+ * has at most D roots); any single changed limb or sign is such an error.
+ * An error that is 0 modulo q (e.g. a sign flipped on a coefficient whose
+ * magnitude is a multiple of q) is never caught.  Layouts as in ipm_mul for `shape` (device
  * pointers).  Waits for `stream`; returns IPM_OK or IPM_ERR_MISMATCH.
  * Allocates and frees a few KB of device memory per call.
  */

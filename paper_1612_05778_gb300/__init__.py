@@ -452,23 +452,50 @@ class TaylorShift:
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
+def output_limbs(na: int, nb: int, bits_a: int, bits_b: int) -> int:
+    """Limbs per output coefficient, Lc = ceil((bits_a + bits_b +
+    ceil(log2 min(na, nb))) / 32): |c_k| <= min(na, nb) (2^bits_a - 1)
+    (2^bits_b - 1) < 2^(bits_a + bits_b + ceil(log2 min(na, nb))).  The
+    planner uses the same formula (ipm_plan_info.lc)."""
+    mn = min(na, nb)
+    lg = (mn - 1).bit_length() if mn > 1 else 0  # ceil(log2 mn)
+    return (bits_a + bits_b + lg + 31) // 32
+
+
+def _check_free_shapes(na, nb, bits_a, bits_b, a, a_neg, b, b_neg, c, c_neg):
+    """Shapes of the operands and of the output of a plan-free call, checked
+    on the host before any pointer is taken or the library is called: a c
+    narrower than Lc limbs would be written past its end by the kernels."""
+    if na < 1 or nb < 1 or bits_a < 1 or bits_b < 1:
+        raise ValueError("need na, nb >= 1 and bit bounds >= 1")
+    la, lb = (bits_a + 31) // 32, (bits_b + 31) // 32
+    nc, lc = na + nb - 1, output_limbs(na, nb, bits_a, bits_b)
+    want = {"a": (a, (na, la)), "a_neg": (a_neg, (na,)), "b": (b, (nb, lb)), "b_neg": (b_neg, (nb,)),
+            "c": (c, (nc, lc)), "c_neg": (c_neg, (nc,))}
+    for name, (t, shape) in want.items():
+        if tuple(t.shape) != shape:
+            raise ValueError("%s must have shape %s, got %s" % (name, shape, tuple(t.shape)))
+    return la, lb, nc, lc
+
+
 def mul_noalloc(na: int, nb: int, bits_a: int, bits_b: int, a, a_neg, b, b_neg, c, c_neg,
                 stream=None):
-    """c = a*b without allocating anything: for callers that may not allocate
-    device memory while they run (stream capture, allocator-free services,
-    plugins whose host owns all memory).  All tensors are caller-owned CUDA
-    tensors (limbs int32 (n, L), signs uint8 (n,)); scratch comes from one
-    static device array shared by every call, so calls must not overlap on
-    the GPU.  Waits for the stream; raises IpmError on failure
-    (IPM_ERR_UNSUPPORTED when the product's scratch exceeds the array)."""
+    """c = a*b without allocating anything, for callers that may not
+    allocate device memory while they run: allocator-free or latency-bound
+    services (cudaMalloc can synchronise the device) and plugins whose host
+    application owns all memory and hands over only the buffers.  All
+    tensors are caller-owned CUDA tensors (limbs int32 (n, L), signs uint8
+    (n,)); c must be (na + nb - 1, output_limbs(...)), checked here before
+    the call.  Scratch comes from one static device array shared by every
+    call; calls are serialised by a host lock and each waits for its
+    stream.  Raises IpmError on failure (IPM_ERR_UNSUPPORTED when the
+    product's scratch exceeds the array)."""
+    la, lb, nc, lc = _check_free_shapes(na, nb, bits_a, bits_b, a, a_neg, b, b_neg, c, c_neg)
     import torch
     lib = load_library()
-    la, lb = (bits_a + 31) // 32, (bits_b + 31) // 32
     args = [_dptr(a, torch.int32, (na, la)), _dptr(a_neg, torch.uint8, (na,)),
             _dptr(b, torch.int32, (nb, lb)), _dptr(b_neg, torch.uint8, (nb,)),
-            _dptr(c, torch.int32), _dptr(c_neg, torch.uint8, (na + nb - 1,))]
-    if c.dim() != 2 or c.shape[0] != na + nb - 1:
-        raise ValueError("c must have na + nb - 1 rows")
+            _dptr(c, torch.int32, (nc, lc)), _dptr(c_neg, torch.uint8, (nc,))]
     _check(lib.ipm_mul_noalloc(ctypes.byref(Shape(na - 1, nb - 1, bits_a, bits_b)), *args,
                                _stream_handle(stream)), "ipm_mul_noalloc")
     return c, c_neg
@@ -476,15 +503,18 @@ def mul_noalloc(na: int, nb: int, bits_a: int, bits_b: int, a, a_neg, b, b_neg, 
 
 def validate(na: int, nb: int, bits_a: int, bits_b: int, a, a_neg, b, b_neg, c, c_neg, seed: int = 1,
              stream=None) -> bool:
-    """ipm_validate: True when c(t) = a(t) b(t) modulo 2^61 - 1 at the
-    point `seed` selects (always for the exact product; a wrong c passes
-    with probability < 2^-40).  CUDA tensors as for Plan.mul; waits."""
+    """ipm_validate: True when c(t) = a(t) b(t) modulo q = 2^61 - 1 at the
+    point `seed` selects.  The exact product always passes.  A wrong c is
+    caught with probability at least 1 - deg(c)/q whenever c - a*b is
+    non-zero modulo q (any single changed limb or sign is); an error that
+    is 0 modulo q is never caught.  CUDA tensors as for Plan.mul, shapes
+    checked on the host first; waits."""
+    la, lb, nc, lc = _check_free_shapes(na, nb, bits_a, bits_b, a, a_neg, b, b_neg, c, c_neg)
     import torch
     lib = load_library()
-    la, lb = (bits_a + 31) // 32, (bits_b + 31) // 32
     args = [_dptr(a, torch.int32, (na, la)), _dptr(a_neg, torch.uint8, (na,)),
             _dptr(b, torch.int32, (nb, lb)), _dptr(b_neg, torch.uint8, (nb,)),
-            _dptr(c, torch.int32), _dptr(c_neg, torch.uint8, (na + nb - 1,))]
+            _dptr(c, torch.int32, (nc, lc)), _dptr(c_neg, torch.uint8, (nc,))]
     st = lib.ipm_validate(ctypes.byref(Shape(na - 1, nb - 1, bits_a, bits_b)), *args,
                           ctypes.c_uint64(seed), _stream_handle(stream))
     if st == 7:
@@ -507,5 +537,5 @@ def to_host(c, c_neg):
 
 
 __all__ = ["Plan", "TaylorShift", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
-           "IPM_SYNC", "IPM_COSTMODEL", "IPM_GRAPH", "IPM_TENSOR_STAGES", "IPM_VALIDATE", "validate", "LIB_PATH", "mul_noalloc", "NOALLOC_SCRATCH_BYTES", "candidates",
+           "IPM_SYNC", "IPM_COSTMODEL", "IPM_GRAPH", "IPM_TENSOR_STAGES", "IPM_VALIDATE", "validate", "LIB_PATH", "mul_noalloc", "output_limbs", "NOALLOC_SCRATCH_BYTES", "candidates",
            "mlp_train", "mlp_grad", "mlp_predict", "set_cost_model", "set_tuned", "dispatch"]

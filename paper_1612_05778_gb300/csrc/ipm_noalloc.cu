@@ -1,11 +1,10 @@
 // ipm_noalloc.cu -- ipm_mul_noalloc: a product that allocates no memory.
 //
 // Who needs it: callers that must not allocate device memory while they
-// run -- code that records a CUDA graph through stream capture (cudaMalloc
-// is not allowed inside a capture), real-time or latency-critical services
-// that forbid allocator calls (cudaMalloc can synchronise the device and
-// take milliseconds), and plugins whose host application owns every
-// allocation and gives the plugin only the input and output buffers.
+// run -- services with latency limits that forbid allocator calls
+// (cudaMalloc can synchronise the device and take milliseconds), and
+// plugins whose host application owns every allocation and gives the
+// plugin only the input and output buffers.
 //
 // How: the error word, the twiddle tables and the transform workspace of
 // one product live in one file-scope device array of fixed size,
@@ -20,9 +19,9 @@
 //    shared-memory limits.  Make that first call before any stream capture.
 //  * All calls share the array, which keeps the previous call's contents.
 //    The error word is cleared and the tables rewritten on every call; the
-//    workspace is fully written before it is read.  Calls that overlap on
-//    the GPU (other streams, other host threads) race on the array: issue
-//    them one after another.
+//    workspace is fully written before it is read.  Calls are serialised
+//    by g_lock, held until the call's stream has finished, so two calls
+//    never overlap on the GPU.
 //  * The call waits for its stream and returns the product's device status.
 #include <cuda_runtime.h>
 
@@ -36,7 +35,7 @@ static __device__ __align__(256) unsigned char g_scratch[IPM_NOALLOC_SCRATCH_BYT
 
 constexpr int kMaxDevices = 64;
 unsigned char *g_scratch_dev[kMaxDevices] = {};   // device address per device
-std::mutex g_lock;                                // guards the host table buffer
+std::mutex g_lock;  // held through the whole call: the host table buffer and the device array
 
 // Host staging for the tables: the largest table set that can fit the
 // device array.  Static storage, so no allocation happens at call time.

@@ -164,3 +164,29 @@ def test_school_plan_fields():
     assert info["K"] == info["r"] == info["Y"] == 0
     assert any(c["params"].get("school") for c in ipm.candidates(300, 257, 255, 255))
     assert not any(c["params"].get("school") for c in ipm.candidates(1 << 15, 1 << 15, 4096, 4096))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_output_limbs_formula_matches_the_planner(shape):
+    assert ipm.output_limbs(*shape) == ipm.choose(*shape)["lc"]
+
+
+def test_plan_free_calls_reject_a_narrow_output_on_the_host():
+    """mul_noalloc and validate check c's shape (nc, Lc) before taking any
+    pointer or calling the library: a c one limb too narrow would be
+    written past its end by the kernels.  CPU tensors suffice, since the
+    check comes first."""
+    torch = pytest.importorskip("torch")
+    na, nb, ba, bb = 300, 200, 255, 100
+    lc = ipm.output_limbs(na, nb, ba, bb)
+    a = torch.zeros((na, 8), dtype=torch.int32)
+    an = torch.zeros((na,), dtype=torch.uint8)
+    b = torch.zeros((nb, 4), dtype=torch.int32)
+    bn = torch.zeros((nb,), dtype=torch.uint8)
+    cn = torch.zeros((na + nb - 1,), dtype=torch.uint8)
+    for bad in [(na + nb - 1, lc - 1), (na + nb - 2, lc), (na + nb - 1,)]:
+        c = torch.zeros(bad, dtype=torch.int32)
+        with pytest.raises(ValueError, match="c must have shape"):
+            ipm.mul_noalloc(na, nb, ba, bb, a, an, b, bn, c, cn)
+        with pytest.raises(ValueError, match="c must have shape"):
+            ipm.validate(na, nb, ba, bb, a, an, b, bn, c, cn)

@@ -90,3 +90,44 @@ def test_byte_slice_dft_identity(p, forward):
             r = (V + m * p) >> 32
             assert (V + m * p) % (1 << 32) == 0 and r < 2 * p
             assert r % p == sum(E[j][k] * x[k] for k in range(16)) % p
+
+
+def _eval_mod_q(coeffs, t):
+    acc = 0
+    for c in reversed(coeffs):
+        acc = (acc * t + c) % Q
+    return acc
+
+
+def test_result_check_catches_errors_nonzero_mod_q_and_misses_multiples_of_q():
+    """What the randomised check can and cannot see: it compares c(t) with
+    a(t) b(t) modulo q, so an error polynomial e = c' - a*b is seen exactly
+    when e(t) != 0 mod q.  A single changed limb adds +-2^(32 l) to one
+    coefficient, never 0 mod q (q is an odd prime), so e is a non-zero
+    polynomial mod q and has at most deg(e) roots; an error that is a
+    multiple of q in every coefficient is invisible at every t."""
+    rng = np.random.default_rng(61)
+    a = [int(v) for v in rng.integers(-2**62, 2**62, 9)]
+    b = [int(v) for v in rng.integers(-2**62, 2**62, 7)]
+    c = [sum(a[i] * b[k - i] for i in range(len(a)) if 0 <= k - i < len(b)) for k in range(len(a) + len(b) - 1)]
+    ts = [int(v) for v in rng.integers(2, Q - 1, 8)]
+    for t in ts:
+        assert _eval_mod_q(c, t) == _eval_mod_q(a, t) * _eval_mod_q(b, t) % Q
+    # one changed limb (limb l of coefficient k): caught at every sampled t
+    for k, l in [(0, 0), (5, 3), (14, 1)]:
+        bad = list(c)
+        bad[k] += 1 << (32 * l)
+        assert (1 << (32 * l)) % Q != 0
+        assert all(_eval_mod_q(bad, t) != _eval_mod_q(a, t) * _eval_mod_q(b, t) % Q for t in ts)
+    # a sign flipped on a coefficient equal to a multiple of q (error -2 c_k,
+    # 0 mod q) and an error of q y^3: never caught
+    bad = list(c)
+    bad[3] += 5 * Q
+    for t in ts:
+        assert _eval_mod_q(bad, t) == _eval_mod_q(c, t)
+    cq = list(c)
+    cq[4] = 7 * Q
+    flipped = list(cq)
+    flipped[4] = -cq[4]
+    for t in ts:
+        assert _eval_mod_q(flipped, t) == _eval_mod_q(cq, t)

@@ -1,8 +1,8 @@
 """ipm_mul_noalloc: the product entry point that allocates nothing.
 
-It serves callers that may not allocate device memory while they run (a
-CUDA graph being recorded by stream capture, allocator-free services,
-plugins whose host owns all memory).  Its scratch is one static device
+It serves callers that may not allocate device memory while they run
+(services that forbid allocator calls because cudaMalloc can synchronise
+the device, plugins whose host application owns all memory).  Its scratch is one static device
 array shared by all calls, so this checks two calls in a row -- the second
 sees the first call's leftovers in the array -- against ipm_mul, the
 allocating entry point, bit for bit (the tolerance of every integer test
