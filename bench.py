@@ -1,14 +1,19 @@
 """Benchmark: exact dense Z[y] products on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload large_dense|small_dense|large_all_ones|huge_dense|huge_mixed|batch|taylor|paper_table]
+                    [--workload huge_dense|large_dense|small_dense|large_all_ones|huge_mixed|batch|taylor|paper_table]
 
 One step is one whole product c = a*b (split, forward 2-D transforms over
 every prime, pointwise products, inverse transforms, CRT, recombination)
-through the C ABI, on the workload of two degree-32767 polynomials with
-4096-bit signed coefficients (seed 1) by default.  Inputs are resident in
-HBM before the timed region; the L2 is flushed (a 512 MiB write) between
-timed steps, outside the events.  Prints ONE JSON line on rank 0.
+through the C ABI, by default on the largest one-GPU workload: two
+polynomials of degree 262143 with 1024-bit signed coefficients (seed 2).
+Inputs are resident in HBM before the timed region; the L2 is flushed (a
+512 MiB write) between timed steps, outside the events.  Prints ONE JSON
+line on rank 0.  The same line carries, under `extras`, the product of two
+degree-32767 polynomials with 4096-bit coefficients (seed 1), the mixed
+variant of the default workload (half the coefficients below 2^64, the rest
+below 2^2048) and the 4096-product batch with its speedup over the plain
+path (--no-extras skips them).
 
 --impl reference times the CPU oracle (plain schoolbook definition, all
 host cores) on a bounded sample of the same workload per step and
@@ -68,7 +73,7 @@ PASS_NAMES = ["k_forward", "k_middle", "k_inverse"]
 E2E_INFLIGHT = 3  # products in flight in the end-to-end measurement
 KERNEL_SRC = [os.path.join(ROOT, "paper_1612_05778_gb300", "csrc", n)
               for n in ("ipm_kernels.cu", "passes.cuh", "ntt_stages.cuh", "modarith.cuh", "ipm_internal.h")]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_large_dense.md")
+DEFAULT_WORKLOAD = "huge_dense"
 
 
 def workload(name: str):
@@ -88,6 +93,11 @@ def workload(name: str):
         sh, a, b = W.huge_mixed(seed=2)
         return ("huge_mixed: d=262144, half the positions < 2^64, the rest < 2^2048, signed, seed 2", sh, a, b)
     raise SystemExit("unknown workload " + name)
+
+
+def workload_config(name, sh):
+    """The `config` of both arms' JSON lines: the workload alone."""
+    return {"workload": name, "na": sh.na, "nb": sh.nb, "bits": sh.bits_a, "lc": sh.lc}
 
 
 # ---------------------------------------------------------------------------
@@ -235,7 +245,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "output_gbit_s": out_bits * value / 1e9,
-        "config": {"workload": name, "na": sh.na, "nb": sh.nb, "bits": sh.bits_a, "lc": sh.lc},
+        "config": workload_config(name, sh),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["threads"], "kind": "oracle",
                          "sample": "per step: %d random output coefficients (%.3g%% of the product's "
                                    "limb products), timed and scaled to one whole product"
@@ -250,14 +260,32 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(info):
-    """Algorithmic DRAM bytes of each pass for one product: forward reads
-    both operands and writes 2 r Y 2K residues; middle reads them and writes
-    r Y 2K; inverse reads r Y 2K and writes the output."""
-    z = info["r"] * info["Y"] * 2 * info["K"] * 4
+def io_bytes(info):
+    """Bytes of the operands (limbs and sign bytes) and of the output."""
     inp = info["na"] * (info["la"] * 4 + 1) + info["nb"] * (info["lb"] * 4 + 1)
     out = info["nc"] * (info["lc"] * 4 + 1)
+    return inp, out
+
+
+def algorithmic_bytes(info):
+    """DRAM bytes each pass of this implementation moves for one product:
+    forward reads both operands and writes 2 r Y 2K residues (both x halves
+    of both operands); middle reads them and writes r Y 2K; inverse reads r
+    Y 2K and writes the output.  With R = r Y K 4 bytes: in + 4R, 6R,
+    2R + out (in + out + 12R in all)."""
+    z = info["r"] * info["Y"] * 2 * info["K"] * 4
+    inp, out = io_bytes(info)
     return [inp + 2 * z, 3 * z, z + out]
+
+
+def schedule_bytes(info):
+    """The three-pass byte count of the method's minimal schedule, R = r Y K
+    4 bytes: forward writes 2R (one K-column slab per operand), middle
+    reads 2R and writes 2R (the product's two x halves), inverse reads 2R:
+    in + 2R, 4R, 2R + out (in + out + 8R in all)."""
+    R = info["r"] * info["Y"] * info["K"] * 4
+    inp, out = io_bytes(info)
+    return [inp + 2 * R, 4 * R, 2 * R + out]
 
 
 # 32-bit integer instructions per algorithmic unit: a lazy
@@ -368,11 +396,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the summary is missing or was taken on other kernel source."""
+def recorded_traffic(kernel: str, workload_name: str):
+    """DRAM bytes per launch of `kernel` on `workload_name` from the
+    committed ncu summary profiles/traffic_<workload>.md, or None when the
+    summary is missing or was taken on other kernel source."""
     try:
-        text = open(TRAFFIC_FILE).read()
+        text = open(os.path.join(ROOT, "profiles", "traffic_%s.md" % workload_name)).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
@@ -382,19 +411,51 @@ def recorded_traffic(kernel: str):
     return int(m.group(1)) if m else None
 
 
-def run_batch(args):
-    """The batched workload: products/s of one ipm_mul_batched call (and of
-    the same products one ipm_mul at a time)."""
-    import torch
-    torch.cuda.set_device(0)
-    from paper_1612_05778_gb300 import build as ipm_build
-    ipm_build.build()
-    import paper_1612_05778_gb300 as ipm
-    shapes = W.batch_shapes(seed=3, count=4096)
-    ops = W.batch_operands(shapes, seed=3)
+BATCH_WORKLOAD = ("batch: 4096 products, degrees log-uniform in [16, 8192], bits log-uniform in [32, 4096], "
+                  "random signs, unbalanced pairs, seed 3")
+
+
+def timed_ms(torch, fn, steps, flush, stream):
+    """Mean event-timed duration of fn() on `stream` over `steps` calls, the
+    L2 flushed (a 512 MiB write) before each call, outside the events."""
+    ms = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.mean(ms))
+
+
+def measure_batch(ipm, torch, steps, warmup, plain_path, flush, rank=0, world=1, dist=None):
+    """One ipm_mul_batched call over the 4096-product batch (seed 3): the
+    chosen form (learned dispatch + graph replay; the analytic planner with
+    plain_path) against the same batch with the analytic planner and the
+    same products as 4096 ipm_mul calls (the plain path).  With world > 1
+    every rank runs its own share of the products (paper_1612_05778_gb300.
+    shard: cost-balanced, no data-path collective) and the times are the
+    maximum over ranks."""
+    from paper_1612_05778_gb300 import shard
+    all_shapes = W.batch_shapes(seed=3, count=4096)
+    all_ops = W.batch_operands(all_shapes, seed=3)
+    mine = list(range(len(all_shapes)))
+    split = None
+    if world > 1:
+        costs = shard.shape_costs([(s.na, s.nb, s.bits_a, s.bits_b) for s in all_shapes])
+        parts = shard.partition(costs, world)
+        mine = parts[rank]
+        ld = shard.loads(costs, parts)
+        split = {"ranks": world, "products_per_rank": [len(p) for p in parts],
+                 "cost_imbalance": max(ld) / (sum(ld) / world)}
+    shapes = [all_shapes[i] for i in mine]
+    ops = [all_ops[i] for i in mine]
     tuples = [(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes]
     flags = 0
-    if not args.plain:
+    if not plain_path:
         from paper_1612_05778_gb300 import costmodel as cmod
         cmod.install(points=cmod.load_sweep()["points"])  # model + the sweep's table
         flags = ipm.IPM_COSTMODEL | ipm.IPM_GRAPH
@@ -404,21 +465,6 @@ def run_batch(args):
     outs = [plan.empty_output(i) for i in range(len(shapes))]
     singles = [ipm.Plan((s.na, s.nb, s.bits_a, s.bits_b)) for s in shapes]
     stream = torch.cuda.current_stream()
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
-
-    def timed(fn, steps):
-        ms = []
-        for _ in range(steps):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        return float(np.mean(ms))
-
     # the timed region holds the C ABI calls; the binding's argument checks
     # and pointer tables are prepared before it (ipm_mul_batched still copies
     # its pointer table to the device on every call)
@@ -437,42 +483,77 @@ def run_batch(args):
             if st:
                 raise SystemExit("ipm_mul failed: %d" % st)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched()
         batched_planner()
         plain()
     torch.cuda.synchronize()
     plan.sync()
     plan_planner.sync()
-    sampler = ClockSampler(0)
-    sampler.start()
-    time.sleep(0.3)
     l0 = ipm.launch_count()
-    ms_b = timed(batched, args.steps)
+    barrier(dist)
+    ms_b = max_over_ranks(dist, timed_ms(torch, batched, steps, flush, stream), torch.cuda.current_device())
     launches = ipm.launch_count() - l0
-    ms_bp = timed(batched_planner, max(1, args.steps // 2))
-    ms_p = timed(plain, max(1, args.steps // 2))
+    ms_bp = max_over_ranks(dist, timed_ms(torch, batched_planner, max(1, steps // 2), flush, stream),
+                           torch.cuda.current_device())
+    ms_p = max_over_ranks(dist, timed_ms(torch, plain, max(1, steps // 2), flush, stream),
+                          torch.cuda.current_device())
     plan_planner.sync()
+    plan.sync()
     changed = sum(any(a[k] != b[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron", "school"))
                   for a, b in zip(plan.infos, plan_planner.infos))
+    n = len(all_shapes)
+    out_bits = sum(s.nc * s.lc * 32 for s in all_shapes)
+    res = {"value": n / (ms_b / 1e3), "unit": UNIT, "ms_per_batch": ms_b, "products": n,
+           "output_gbit_s": out_bits / (ms_b / 1e3) / 1e9, "speedup_vs_plain": ms_p / ms_b,
+           "plain": {"ms_per_batch": ms_p, "value": n / (ms_p / 1e3),
+                     "path": "one ipm_mul C call per product (pointers prepared), analytic planner"},
+           "batched_planner": {"ms_per_batch": ms_bp, "value": n / (ms_bp / 1e3),
+                               "path": "one ipm_mul_batched call, analytic planner"},
+           "dispatch": {"flags": "IPM_COSTMODEL | IPM_GRAPH" if flags else "none (--plain)",
+                        "products_with_another_plan": int(changed)},
+           "workload": BATCH_WORKLOAD, "gpu_launches": int(launches), "launches_per_call": launches / steps,
+           "split": split}
+    for sp in singles:
+        sp.close()
+    plan.close()
+    plan_planner.close()
+    return res
+
+
+def run_batch(args):
+    """The batched workload alone: products/s of one ipm_mul_batched call
+    (and of the same products one ipm_mul at a time).  Under torchrun the
+    4096 products are split across the ranks (strong scaling: the total
+    work is fixed)."""
+    import torch
+    world, rank, local = dist_env()
+    dist = dist_init(world, "nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1612_05778_gb300 import build as ipm_build
+    if rank == 0:
+        ipm_build.build()
+    barrier(dist)
+    import paper_1612_05778_gb300 as ipm
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    r = measure_batch(ipm, torch, args.steps, args.warmup, args.plain, flush, rank, world, dist)
     clocks = sampler.stop()
-    n = len(shapes)
-    out_bits = sum(s.nc * s.lc * 32 for s in shapes)
-    line = {"metric": METRIC, "value": n / (ms_b / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_batch"], "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "split": r["split"],
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "output_gbit_s": out_bits / (ms_b / 1e3) / 1e9,
-            "speedup_vs_plain": ms_p / ms_b,
-            "plain": {"ms_per_batch": ms_p, "value": n / (ms_p / 1e3),
-                      "path": "one ipm_mul C call per product (pointers prepared), analytic planner"},
-            "batched_planner": {"ms_per_batch": ms_bp, "value": n / (ms_bp / 1e3),
-                                "path": "one ipm_mul_batched call, analytic planner"},
-            "dispatch": {"flags": "IPM_COSTMODEL | IPM_GRAPH" if flags else "none (--plain)",
-                         "products_with_another_plan": int(changed)},
-            "config": {"workload": "batch: 4096 products, degrees log-uniform in [16, 8192], bits log-uniform "
-                                   "in [32, 4096], random signs, unbalanced pairs, seed 3",
-                       "products": len(plan.infos), "l2": "flushed between timed steps"},
-            "gpu_launches": int(launches), "launches_per_step": launches / args.steps, "clocks": clocks}
+            "output_gbit_s": r["output_gbit_s"], "speedup_vs_plain": r["speedup_vs_plain"],
+            "plain": r["plain"], "batched_planner": r["batched_planner"], "dispatch": r["dispatch"],
+            "config": {"workload": BATCH_WORKLOAD},
+            "setup": {"products": r["products"], "l2": "flushed between timed steps"},
+            "gpu_launches": r["gpu_launches"], "launches_per_step": r["launches_per_call"], "clocks": clocks}
     print(json.dumps(line))
     return 0
 
@@ -625,6 +706,128 @@ def run_paper_table(args):
     return 0
 
 
+PLAN_KEYS = ("K", "M", "N", "r", "Y", "Y1", "Y2", "S", "Y1b", "kron", "school")
+
+
+def chosen_flags(ipm, shape, plain_path):
+    """The chosen form's plan flags for one product: the learned dispatch
+    (committed GB300 cost model and the sweep's table of measured bests),
+    or none with plain_path (the analytic planner)."""
+    if plain_path:
+        return 0, {"source": "planner (--plain)", "params": {}}
+    from paper_1612_05778_gb300 import costmodel as cmod
+    cmod.install(points=cmod.load_sweep()["points"])
+    prm, src = ipm.dispatch(*shape)
+    return ipm.IPM_COSTMODEL, {"source": src, "params": prm}
+
+
+def roofline_of(info, pass_avg, sm_max, traffic_workload=None):
+    """Roofline of the dominant pass: its algorithmic integer operations and
+    its bytes over its event-timed duration.  The main entry is the bound
+    with the larger fraction; beside it the HBM fraction on the method's
+    minimal three-pass byte count (in + out + 8R per product, R = r Y K 4)
+    and on this implementation's byte count (in + out + 12R), and the same
+    two for the whole product."""
+    dom = int(np.argmax(pass_avg))
+    sbytes, ibytes = schedule_bytes(info), algorithmic_bytes(info)
+    aops = algorithmic_int_ops(info)
+    peak, peak_kind = load_peak_hbm()
+    alu_peak = alu_peak_tops(sm_max)
+    secs = pass_avg[dom] / 1e3
+    alu_ach = aops[dom] / secs / 1e12
+    hbm_s = sbytes[dom] / secs / 1e9
+    hbm_i = ibytes[dom] / secs / 1e9
+    alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s (int32)",
+           "frac": alu_ach / alu_peak, "peak_kind": "derived: 152 SMs x 128 int32 lanes x %.0f MHz" % sm_max}
+    hbm = {"bound": "hbm", "achieved": hbm_s, "peak": peak, "unit": "GB/s", "frac": hbm_s / peak,
+           "peak_kind": peak_kind + " (burst copy, MEASURED_PEAKS.json)"}
+    main = alu if alu["frac"] >= hbm["frac"] else hbm
+    traffic = recorded_traffic(PASS_NAMES[dom], traffic_workload) if traffic_workload else None
+    roof = dict(main)
+    total_ms = float(np.sum(pass_avg))
+    roof.update({
+        "kernel": PASS_NAMES[dom], "traffic": traffic,
+        "algorithmic_int_ops": aops[dom],
+        "hbm": {
+            "schedule_bytes": {"bytes": sbytes[dom], "achieved": hbm_s, "peak": peak, "unit": "GB/s",
+                               "frac": hbm_s / peak,
+                               "what": "the method's three-pass schedule: K1 in + 2R, K2 4R, K3 2R + out"},
+            "implementation_bytes": {"bytes": ibytes[dom], "achieved": hbm_i, "peak": peak, "unit": "GB/s",
+                                     "frac": hbm_i / peak,
+                                     "what": "this implementation: K1 in + 4R, K2 6R, K3 2R + out"},
+            "traffic_over_schedule_bytes": (traffic / sbytes[dom]) if traffic else None},
+        "product": {"schedule_bytes": sum(sbytes), "implementation_bytes": sum(ibytes), "ms": total_ms,
+                    "schedule_frac": sum(sbytes) / (total_ms / 1e3) / 1e9 / peak,
+                    "implementation_frac": sum(ibytes) / (total_ms / 1e3) / 1e9 / peak,
+                    "alu_frac": sum(aops) / (total_ms / 1e3) / 1e12 / alu_peak},
+    })
+    return roof
+
+
+def measure_product(ipm, torch, key, plain_path, steps, warmup, flush, stream, keep=False):
+    """One product of workload `key` through ipm_mul with the chosen form's
+    plan: event-timed steps (L2 flushed between them), per-pass times, and
+    the analytic planner's plan timed beside it when it differs (outputs
+    must agree byte for byte)."""
+    name, sh, a, b = workload(key)
+    shape = (sh.na, sh.nb, sh.bits_a, sh.bits_b)
+    flags, dispatch = chosen_flags(ipm, shape, plain_path)
+    plan = ipm.Plan(shape, flags=flags)
+    info = plan.info
+    plain_plan = ipm.Plan(shape)
+    same_plan = all(plain_plan.info[k] == info[k] for k in PLAN_KEYS)
+    da, dan = ipm.to_device(*a)
+    db, dbn = ipm.to_device(*b)
+    c, cn = plan.empty_output()
+    plan.mul(da, dan, db, dbn, c, cn)
+    plan.sync()
+    for _ in range(warmup):
+        plan.mul(da, dan, db, dbn, c, cn)
+    torch.cuda.synchronize()
+    plan.set_profiling(True)
+    step_ms, pass_ms = [], np.zeros(3)
+    l0 = ipm.launch_count()
+    for _ in range(steps):
+        step_ms.append(timed_ms(torch, lambda: plan.mul(da, dan, db, dbn, c, cn, stream=stream), 1, flush, stream))
+        pass_ms += np.array(plan.phase_ms())
+    launches = ipm.launch_count() - l0
+    plan.set_profiling(False)
+    plan.sync()
+    plain_ms = None
+    if not same_plan:
+        c2, cn2 = plain_plan.empty_output()
+        for _ in range(warmup):
+            plain_plan.mul(da, dan, db, dbn, c2, cn2)
+        plain_ms = timed_ms(torch, lambda: plain_plan.mul(da, dan, db, dbn, c2, cn2, stream=stream),
+                            max(3, steps // 2), flush, stream)
+        plain_plan.sync()
+        if not (torch.equal(c, c2) and torch.equal(cn, cn2)):
+            raise SystemExit("chosen and plain plans disagree on " + key)
+        del c2, cn2
+    plain_plan.close()
+    ms = float(np.mean(step_ms))
+    res = {"name": name, "shape": sh, "info": info, "flags": flags, "dispatch": dispatch,
+           "step_ms": step_ms, "ms": ms, "value": 1e3 / ms, "pass_avg": pass_ms / steps,
+           "plain_ms": plain_ms, "speedup_vs_plain": (plain_ms / ms) if plain_ms else 1.0,
+           "launches": launches, "output_gbit_s": sh.nc * sh.lc * 32 / (ms / 1e3) / 1e9}
+    if keep:
+        res.update({"plan": plan, "a": a, "b": b, "dev": (da, dan, db, dbn), "out": (c, cn)})
+    else:
+        plan.close()
+    return res
+
+
+def product_summary(r, sm_max):
+    """The extra-workload entry of the JSON line."""
+    info = r["info"]
+    return {"workload": r["name"], "value": r["value"], "unit": UNIT, "ms_per_product": r["ms"],
+            "output_gbit_s": r["output_gbit_s"], "speedup_vs_plain": r["speedup_vs_plain"],
+            "plain_ms": r["plain_ms"],
+            "passes_ms": {PASS_NAMES[i]: float(r["pass_avg"][i]) for i in range(3)},
+            "plan": {k: info[k] for k in PLAN_KEYS}, "dispatch": r["dispatch"],
+            "roofline": roofline_of(info, r["pass_avg"], sm_max)}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -637,86 +840,27 @@ def run_ours(args):
     barrier(dist)
     import paper_1612_05778_gb300 as ipm
 
-    name, sh, a, b = workload(args.workload)
-    shape = (sh.na, sh.nb, sh.bits_a, sh.bits_b)
-    # the chosen form: the plan the learned dispatch picks (committed GB300
-    # cost model); --plain forces the analytic planner's plan
-    flags = 0
-    dispatch = {"source": "planner (--plain)", "params": {}}
-    if not args.plain:
-        from paper_1612_05778_gb300 import costmodel as cmod
-        cmod.install(points=cmod.load_sweep()["points"])  # model + the sweep's table
-        flags = ipm.IPM_COSTMODEL
-        prm, src = ipm.dispatch(*shape)
-        dispatch = {"source": src, "params": prm}
-    plan = ipm.Plan(shape, flags=flags)
-    info = plan.info
-    plain_plan = ipm.Plan(shape)
-    same_plan = all(plain_plan.info[k] == info[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron", "school"))
-    da, dan = ipm.to_device(*a)
-    db, dbn = ipm.to_device(*b)
-    c, cn = plan.empty_output()
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
-
-    # correctness guard on the benchmarked plan: two sampled coefficients
-    plan.mul(da, dan, db, dbn, c, cn)
-    plan.sync()
-
-    for _ in range(args.warmup):
-        plan.mul(da, dan, db, dbn, c, cn)
-    torch.cuda.synchronize()
-
-    plan.set_profiling(True)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     barrier(dist)
     torch.cuda.synchronize()
-    launches0 = ipm.launch_count()
-    step_ms = []
-    pass_ms = np.zeros(3)
     t_wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plan.mul(da, dan, db, dbn, c, cn, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        pass_ms += np.array(plan.phase_ms())
+    main_r = measure_product(ipm, torch, args.workload, args.plain, args.steps, args.warmup, flush, stream,
+                             keep=True)
     torch.cuda.synchronize()
     barrier(dist)
     wall = time.perf_counter() - t_wall0
-    launches = ipm.launch_count() - launches0
     clocks = sampler.stop()
-    plan.set_profiling(False)
-    plan.sync()
-
-    # the plain path (analytic planner) on the same inputs, when it differs
-    plain_ms = None
-    if not same_plan:
-        c2, cn2 = plain_plan.empty_output()
-        for _ in range(args.warmup):
-            plain_plan.mul(da, dan, db, dbn, c2, cn2)
-        pm = []
-        for _ in range(max(3, args.steps // 2)):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            plain_plan.mul(da, dan, db, dbn, c2, cn2, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            pm.append(e0.elapsed_time(e1))
-        plain_plan.sync()
-        if not (torch.equal(c, c2) and torch.equal(cn, cn2)):
-            raise SystemExit("chosen and plain plans disagree")
-        plain_ms = float(np.mean(pm))
-        del c2, cn2
-    plain_plan.close()
+    name, sh, info, plan = main_r["name"], main_r["shape"], main_r["info"], main_r["plan"]
+    a, b = main_r["a"], main_r["b"]
+    da, dan, db, dbn = main_r["dev"]
+    c, cn = main_r["out"]
+    flags = main_r["flags"]
+    shape = (sh.na, sh.nb, sh.bits_a, sh.bits_b)
+    step_ms = main_r["step_ms"]
 
     # the same plan with every radix-16 stage on the INT8 tensor cores
     # (IPM_TENSOR_STAGES), timed on the same inputs; its output must be
@@ -734,14 +878,8 @@ def run_ours(args):
         tm, tpass = [], np.zeros(3)
         nt = max(3, args.steps // 2)
         for _ in range(nt):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            tplan.mul(da, dan, db, dbn, c3, cn3, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            tm.append(e0.elapsed_time(e1))
+            tm.append(timed_ms(torch, lambda: tplan.mul(da, dan, db, dbn, c3, cn3, stream=stream), 1, flush,
+                               stream))
             tpass += np.array(tplan.phase_ms())
         tplan.set_profiling(False)
         tplan.sync()
@@ -749,7 +887,7 @@ def run_ours(args):
         tops = tensor_stage_ops(tplan.info, sh.na, sh.nb)
         t_ms = float(np.mean(tm))
         tensor = {"ms_per_step": t_ms, "value": 1e3 / t_ms,
-                  "ratio_to_integer_stages": float(np.sum(step_ms) / args.steps) / t_ms,
+                  "ratio_to_integer_stages": float(np.mean(step_ms)) / t_ms,
                   "passes_ms": {PASS_NAMES[i]: float(tpass[i]) for i in range(3)},
                   "int8_tensor_ops": int(sum(tops)),
                   "int8_tensor": {"achieved": sum(tops) / (t_ms / 1e3) / 1e12, "peak": INT8_MMA_SYNC_TOPS,
@@ -767,32 +905,13 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms / 1e3)
     out_bits = sh.nc * sh.lc * 32
-
-    # roofline of the dominant pass: algorithmic bytes and algorithmic
-    # integer operations over its event-timed duration; the bound reported
-    # is the one with the larger fraction
-    pass_avg = pass_ms / args.steps
-    dom = int(np.argmax(pass_avg))
-    abytes = algorithmic_bytes(info)
-    aops = algorithmic_int_ops(info)
-    peak, peak_kind = load_peak_hbm()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    alu_peak = alu_peak_tops(sm_max)
-    secs = pass_avg[dom] / 1e3
-    hbm_ach = abytes[dom] / secs / 1e9
-    alu_ach = aops[dom] / secs / 1e12
-    hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": peak, "unit": "GB/s", "frac": hbm_ach / peak,
-           "peak_kind": peak_kind + " (burst copy, MEASURED_PEAKS.json)"}
-    alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s (int32)",
-           "frac": alu_ach / alu_peak, "peak_kind": "derived: 152 SMs x 128 int32 lanes x %.0f MHz" % sm_max}
-    main = alu if alu["frac"] >= hbm["frac"] else hbm
-    other = hbm if main is alu else alu
-    roofline = dict(main)
-    roofline.update({"kernel": PASS_NAMES[dom], "traffic": recorded_traffic(PASS_NAMES[dom]),
-                     "algorithmic_bytes": abytes[dom], "algorithmic_int_ops": aops[dom],
-                     "other": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
-    passes = {PASS_NAMES[i]: {"ms": float(pass_avg[i]), "algorithmic_bytes": abytes[i],
-                              "gbs": abytes[i] / (pass_avg[i] / 1e3) / 1e9,
+    pass_avg = main_r["pass_avg"]
+    roofline = roofline_of(info, pass_avg, sm_max, traffic_workload=args.workload)
+    sbytes, abytes, aops = schedule_bytes(info), algorithmic_bytes(info), algorithmic_int_ops(info)
+    passes = {PASS_NAMES[i]: {"ms": float(pass_avg[i]), "schedule_bytes": sbytes[i],
+                              "implementation_bytes": abytes[i],
+                              "gbs_implementation": abytes[i] / (pass_avg[i] / 1e3) / 1e9,
                               "algorithmic_int_ops": aops[i],
                               "int_tops": aops[i] / (pass_avg[i] / 1e3) / 1e12} for i in range(3)}
 
@@ -801,7 +920,7 @@ def run_ours(args):
     # the timed region; E2E_INFLIGHT plans on as many streams keep that many
     # products in flight so their copies overlap the others' compute
     # (ipm_mul_host_async; measured on a GB300: 699 products/s with two,
-    # 765 with three, 765 with four)
+    # 765 with three, 765 with four on d = 32768, 4096-bit)
     e2e = None
     if not args.no_e2e:
         pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()  # noqa: E731
@@ -828,6 +947,9 @@ def run_ours(args):
         dt = max_over_ranks(dist, time.perf_counter() - t0, dev)
         if not all(np.array_equal(outs[0][0], o[0]) and np.array_equal(outs[0][1], o[1]) for o in outs[1:]):
             raise SystemExit("end-to-end products disagree")
+        if not (np.array_equal(outs[0][0], c.cpu().numpy().view(np.uint32)) and
+                np.array_equal(outs[0][1], cn.cpu().numpy())):
+            raise SystemExit("end-to-end product differs from the device-resident one")
         h2d = ha.nbytes + han.nbytes + hb.nbytes + hbn.nbytes
         d2h = outs[0][0].nbytes + outs[0][1].nbytes
         e2e = {"value": world * n_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -836,6 +958,22 @@ def run_ours(args):
                       "product, copies out), then ipm_sync; host wall clock" % (nf, nf)}
         for pl in plans:
             pl.close()
+        del ha, han, hb, hbn, outs
+    del da, dan, db, dbn, c, cn
+    plan.close()
+    torch.cuda.empty_cache()
+
+    # the other configurations, as extra keys of the same line (rank 0)
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        for key in ("large_dense", "huge_mixed"):
+            if key == args.workload:
+                continue
+            r = measure_product(ipm, torch, key, args.plain, max(5, args.steps // 2), 3, flush, stream)
+            extras[key] = product_summary(r, sm_max)
+            torch.cuda.empty_cache()
+        extras["batch"] = measure_batch(ipm, torch, max(3, args.steps // 4), 3, args.plain, flush)
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -850,29 +988,29 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "output_gbit_s": out_bits * value / 1e9,
-        "speedup_vs_plain": (plain_ms / (local_ms / args.steps)) if plain_ms else 1.0,
-        "plain": ({"ms_per_step": plain_ms, "path": "analytic planner's plan"} if plain_ms else
+        "speedup_vs_plain": main_r["speedup_vs_plain"],
+        "plain": ({"ms_per_step": main_r["plain_ms"], "path": "analytic planner's plan"} if main_r["plain_ms"] else
                   {"path": "the analytic planner picks the same plan: one path, ratio 1"}),
-        "config": {"workload": name, "na": sh.na, "nb": sh.nb, "bits": sh.bits_a, "lc": sh.lc,
-                   "plan": {k: info[k] for k in ("K", "M", "N", "r", "Y", "Y1", "Y2", "S", "Y1b", "kron", "school")},
-                   "dispatch": dispatch,
-                   "primes": info["primes"], "parallelism": "replicas (one product per GPU)",
-                   "l2": "flushed between timed steps (512 MiB write, outside the events)",
-                   "path": "2-D NTT (Shoup butterflies), %d launches per product" % (
-                       3 + (2 if info["Y1b"] > 1 else 0))},
+        "config": workload_config(name, sh),
+        "setup": {"plan": {k: info[k] for k in PLAN_KEYS}, "dispatch": main_r["dispatch"],
+                  "primes": info["primes"], "parallelism": "replicas (one product per GPU)",
+                  "l2": "flushed between timed steps (512 MiB write, outside the events)",
+                  "path": "2-D NTT (Shoup butterflies), %d launches per product" % (
+                      3 + (2 if info["Y1b"] > 1 else 0))},
         "roofline": roofline,
         "passes": passes,
         "tensor_stages": tensor,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": int(launches),
-        "launches_per_step": launches / args.steps,
+        "extras": extras,
+        "batch_speedup_vs_plain": extras["batch"]["speedup_vs_plain"] if "batch" in extras else None,
+        "gpu_launches": int(main_r["launches"]),
+        "launches_per_step": main_r["launches"] / args.steps,
         "clocks": clocks,
         "wall_s_timed": wall,
     }
     if rank == 0:
         print(json.dumps(line))
-    plan.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -884,7 +1022,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="large_dense")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations (d=32768 4096-bit, the mixed d=262144 variant, the batch)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain", action="store_true",
                     help="the plain path: analytic planner only, no learned dispatch")
@@ -897,7 +1037,7 @@ def main(argv=None):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("batch", "taylor", "paper_table"):
+    if args.workload in ("taylor", "paper_table"):
         # one-GPU measurements: under torchrun only rank 0 runs them
         world, rank, _ = dist_env()
         if world > 1 and rank != 0:

@@ -6,7 +6,9 @@ import it; the two share no code.
 
 The oracle is the plain definition c_k = sum_{i+j=k} a_i b_j over Z (§1 and
 §2 of arXiv 1612.05778), computed by ``ipm_oracle.c`` with its own bigint
-(schoolbook limb products into signed accumulators).  ``build()`` compiles it
+(schoolbook limb products into signed accumulators); for full outputs at
+large sizes the same c is read off the integer product a(2^s) b(2^s)
+(Kronecker substitution) done with the oracle's own Karatsuba.  ``build()`` compiles it
 with gcc into ``liboracle.so`` next to this file.
 """
 from __future__ import annotations
@@ -47,6 +49,10 @@ def _load():
             lib.orc_polymul_mut.restype = ctypes.c_int
             lib.orc_coeffs.argtypes = [i64, P, i64, i32, P, P, i64, i32, P, P, i32, P, P, i32]
             lib.orc_coeffs.restype = ctypes.c_int
+            lib.orc_polymul_kron.argtypes = [i64, i32, P, P, i64, i32, P, P, i32, P, P, i32]
+            lib.orc_polymul_kron.restype = ctypes.c_int
+            lib.orc_kara_mul.argtypes = [i64, P, P, P, i32]
+            lib.orc_kara_mul.restype = ctypes.c_int
             lib.orc_eval_mod.argtypes = [i64, i32, P, P, ctypes.c_uint64, ctypes.c_uint64]
             lib.orc_eval_mod.restype = ctypes.c_uint64
             _lib = lib
@@ -82,6 +88,39 @@ def polymul(a, b, lc: int, threads: int | None = None, mutation: int = 0):
     if st != 0:
         raise RuntimeError("oracle polymul failed with status %d" % st)
     return c, cn
+
+
+def polymul_kron(a, b, lc: int, threads: int | None = None):
+    """Full product c = a*b by Kronecker substitution (a(2^s) b(2^s), slots
+    of s = 32 (lc + 1) bits) and the oracle's own threaded Karatsuba; the
+    same result as polymul, for sizes where the schoolbook is out of
+    reach.  Returns (limbs (na+nb-1, lc) u32, neg u8)."""
+    (al, an), (bl, bn) = _prep(*a), _prep(*b)
+    na, la = al.shape
+    nb, lb = bl.shape
+    nc = na + nb - 1
+    c = np.zeros((nc, lc), dtype=np.uint32)
+    cn = np.zeros(nc, dtype=np.uint8)
+    st = _load().orc_polymul_kron(na, la, _ptr(al), _ptr(an), nb, lb, _ptr(bl), _ptr(bn),
+                                  lc, _ptr(c), _ptr(cn), threads or default_threads())
+    if st != 0:
+        raise RuntimeError("oracle polymul_kron failed with status %d" % st)
+    return c, cn
+
+
+def kara_mul(x: int, y: int, threads: int = 1) -> int:
+    """x * y for non-negative Python integers through the oracle's
+    Karatsuba (the integer product inside polymul_kron)."""
+    n = max(x.bit_length(), y.bit_length(), 1)
+    n32 = (n + 31) // 32
+    n32 += n32 & 1
+    xa = np.frombuffer(x.to_bytes(4 * n32, "little"), dtype=np.uint32).copy()
+    ya = np.frombuffer(y.to_bytes(4 * n32, "little"), dtype=np.uint32).copy()
+    r = np.zeros(2 * n32, dtype=np.uint32)
+    st = _load().orc_kara_mul(n32, _ptr(xa), _ptr(ya), _ptr(r), threads)
+    if st != 0:
+        raise RuntimeError("oracle kara_mul failed with status %d" % st)
+    return int.from_bytes(r.tobytes(), "little")
 
 
 def coeffs(ks, a, b, lc: int, threads: int | None = None):

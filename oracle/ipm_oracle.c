@@ -303,3 +303,272 @@ uint64_t orc_eval_mod(int64_t n, int32_t l, const uint32_t *x, const uint8_t *ne
     }
     return acc;
 }
+
+/* ======================================================================
+ * Full outputs at large sizes: Kronecker substitution (§1: the product of
+ * two polynomials is read off the product of the integers a(2^s), b(2^s))
+ * with the oracle's own Karatsuba integer multiplication (A. Karatsuba,
+ * Yu. Ofman, "Multiplication of multidigit numbers on automata", 1962).
+ *
+ *   A = a(2^s) = sum_i a_i 2^(s i),  B = b(2^s),  C = A B = sum_k c_k 2^(s k)
+ *
+ * with slots of s = 32 (lc + 1) bits: |c_k| < 2^(32 lc) <= 2^(s-1), so the
+ * signed slots of C are read back exactly (a slot value t, plus the
+ * borrow of the slot below, is c_k when below 2^(s-1) and c_k + 2^s with a
+ * borrow of one into the next slot otherwise).  Schoolbook on the full
+ * cfg sizes is out of reach (about 10^13 limb products); this is the
+ * definition of c evaluated at 2^s, with the integer product done by
+ * Karatsuba's three half-size products.  Pinned against the schoolbook
+ * oracle and Python integers in tests/test_oracle_pins.py.
+ * ====================================================================== */
+
+typedef unsigned __int128 u128;
+#define KARA_BASE 32   /* schoolbook below this many 64-bit limbs */
+
+/* r[0..2n) = a[0..n) * b[0..n), schoolbook on 64-bit limbs */
+static void school64(uint64_t *r, const uint64_t *a, const uint64_t *b, int64_t n) {
+    memset(r, 0, (size_t)(2 * n) * 8);
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t carry = 0;
+        const u128 ai = a[i];
+        for (int64_t j = 0; j < n; ++j) {
+            u128 t = ai * b[j] + r[i + j] + carry;
+            r[i + j] = (uint64_t)t;
+            carry = (uint64_t)(t >> 64);
+        }
+        r[i + n] = carry;
+    }
+}
+
+/* r[0..n) = x[0..n) + y[0..n); returns the carry */
+static uint64_t add64(uint64_t *r, const uint64_t *x, const uint64_t *y, int64_t n) {
+    uint64_t c = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        u128 t = (u128)x[k] + y[k] + c;
+        r[k] = (uint64_t)t;
+        c = (uint64_t)(t >> 64);
+    }
+    return c;
+}
+
+/* r[0..n) = x[0..n) - y[0..n); returns the borrow */
+static uint64_t sub64(uint64_t *r, const uint64_t *x, const uint64_t *y, int64_t n) {
+    uint64_t b = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        uint64_t xk = x[k], yk = y[k];
+        uint64_t d = xk - yk - b;
+        b = (xk < yk) || (xk == yk && b) ? 1 : 0;
+        r[k] = d;
+    }
+    return b;
+}
+
+/* adds x[0..n) into r[0..len) (len >= n), carrying upward */
+static void add_into(uint64_t *r, int64_t len, const uint64_t *x, int64_t n) {
+    uint64_t c = add64(r, r, x, n);
+    for (int64_t k = n; c && k < len; ++k) {
+        r[k] += 1;
+        c = r[k] == 0;
+    }
+}
+
+/* |x - y| for x of nx limbs and y of ny limbs (nx, ny <= n), zero-extended
+ * to n limbs, into d[0..n); returns 1 when x < y */
+static int absdiff(uint64_t *d, const uint64_t *x, int64_t nx, const uint64_t *y, int64_t ny, int64_t n) {
+    int64_t k;
+    int cmp = 0;
+    for (k = n - 1; k >= 0; --k) {
+        uint64_t xk = k < nx ? x[k] : 0, yk = k < ny ? y[k] : 0;
+        if (xk != yk) { cmp = xk < yk ? -1 : 1; break; }
+    }
+    const uint64_t *hi = cmp < 0 ? y : x, *lo = cmp < 0 ? x : y;
+    int64_t nh = cmp < 0 ? ny : nx, nl = cmp < 0 ? nx : ny;
+    uint64_t b = 0;
+    for (k = 0; k < n; ++k) {
+        uint64_t hk = k < nh ? hi[k] : 0, lk = k < nl ? lo[k] : 0;
+        uint64_t dk = hk - lk - b;
+        b = (hk < lk) || (hk == lk && b) ? 1 : 0;
+        d[k] = dk;
+    }
+    return cmp < 0;
+}
+
+typedef struct {
+    uint64_t *r;
+    const uint64_t *a, *b;
+    int64_t n;
+    int depth;  /* levels that still run their three products on threads */
+    int status;
+} kara_job;
+
+static int kara(uint64_t *r, const uint64_t *a, const uint64_t *b, int64_t n, uint64_t *tmp, int depth);
+
+static void *kara_thread(void *arg) {
+    kara_job *J = (kara_job *)arg;
+    uint64_t *tmp = (uint64_t *)malloc((size_t)(4 * J->n + 256) * 8);
+    if (!tmp) { J->status = -3; return NULL; }
+    J->status = kara(J->r, J->a, J->b, J->n, tmp, J->depth);
+    free(tmp);
+    return NULL;
+}
+
+/*
+ * r[0..2n) = a[0..n) * b[0..n).  With h = floor(n/2), m = n - h and
+ * a = a0 + a1 W^h, b = b0 + b1 W^h (W = 2^64):
+ *     a b = z0 + (z0 + z2 + s |a0 - a1| |b1 - b0|) W^h + z2 W^(2h),
+ * z0 = a0 b0, z2 = a1 b1, s the sign of (a0 - a1)(b1 - b0): the middle
+ * term is a0 b1 + a1 b0 >= 0.  tmp holds at least 4 n + 64 limbs.
+ */
+static int kara(uint64_t *r, const uint64_t *a, const uint64_t *b, int64_t n, uint64_t *tmp, int depth) {
+    if (n <= KARA_BASE) {
+        school64(r, a, b, n);
+        return 0;
+    }
+    const int64_t h = n / 2, m = n - h;
+    uint64_t *da = tmp, *db = tmp + m, *p = tmp + 2 * m, *rest = tmp + 4 * m;
+    const int na_neg = absdiff(da, a, h, a + h, m, m);   /* |a0 - a1| */
+    const int nb_neg = absdiff(db, b + h, m, b, h, m);   /* |b1 - b0| */
+    const int neg = na_neg ^ nb_neg;
+    int st = 0;
+    if (depth > 0) {
+        kara_job J[3] = {{r, a, b, h, depth - 1, 0}, {r + 2 * h, a + h, b + h, m, depth - 1, 0},
+                         {p, da, db, m, depth - 1, 0}};
+        pthread_t tid[2];
+        int started[2] = {0, 0};
+        for (int q = 0; q < 2; ++q) started[q] = pthread_create(&tid[q], NULL, kara_thread, &J[q]) == 0;
+        kara_thread(&J[2]);
+        for (int q = 0; q < 2; ++q) {
+            if (started[q]) pthread_join(tid[q], NULL);
+            else kara_thread(&J[q]);
+        }
+        for (int q = 0; q < 3; ++q) if (J[q].status) st = J[q].status;
+        if (st) return st;
+    } else {
+        st = kara(r, a, b, h, rest, 0);                 /* z0 in r[0, 2h) */
+        if (!st) st = kara(r + 2 * h, a + h, b + h, m, rest, 0);  /* z2 in r[2h, 2n) */
+        if (!st) st = kara(p, da, db, m, rest, 0);      /* |a0-a1| |b1-b0| */
+        if (st) return st;
+    }
+    /* t = z0 + z2 +- p, 2m + 1 limbs (non-negative) */
+    uint64_t *t = rest;
+    memcpy(t, r + 2 * h, (size_t)(2 * m) * 8);
+    t[2 * m] = 0;
+    add_into(t, 2 * m + 1, r, 2 * h);
+    if (neg) {
+        uint64_t bw = sub64(t, t, p, 2 * m);
+        t[2 * m] -= bw;
+    } else {
+        add_into(t, 2 * m + 1, p, 2 * m);
+    }
+    add_into(r + h, 2 * n - h, t, 2 * m + 1 <= 2 * n - h ? 2 * m + 1 : 2 * n - h);
+    return 0;
+}
+
+/* Product of two non-negative integers of n 32-bit limbs each (n even),
+ * r of 2n limbs: Karatsuba over 64-bit limbs (little-endian pairs). */
+int orc_kara_mul(int64_t n32, const uint32_t *a, const uint32_t *b, uint32_t *r, int32_t nthreads) {
+    if (n32 < 1 || (n32 & 1)) return -1;
+    const int64_t n = n32 / 2;
+    uint64_t *A = (uint64_t *)malloc((size_t)n * 8), *B = (uint64_t *)malloc((size_t)n * 8);
+    uint64_t *R = (uint64_t *)malloc((size_t)(2 * n) * 8);
+    uint64_t *tmp = (uint64_t *)malloc((size_t)(4 * n + 256) * 8);
+    int st = -3;
+    if (A && B && R && tmp) {
+        memcpy(A, a, (size_t)n32 * 4);  /* little-endian u32 pairs are u64 limbs */
+        memcpy(B, b, (size_t)n32 * 4);
+        int depth = 0;
+        for (int64_t w = 1; w < nthreads && depth < 5; w *= 3) ++depth;
+        st = kara(R, A, B, n, tmp, depth);
+        if (!st) memcpy(r, R, (size_t)(2 * n32) * 4);
+    }
+    free(A); free(B); free(R); free(tmp);
+    return st;
+}
+
+/* Packs the signed coefficients x (n rows of l limbs, signs xn) into
+ * X = sum_i x_i 2^(32 w i) as a sign-magnitude integer of `len` 32-bit
+ * limbs (len >= n w + 1, even); returns the sign (1 negative). */
+static int pack_signed(uint32_t *X, int64_t len, const uint32_t *x, const uint8_t *xn, int64_t n, int32_t l,
+                       int32_t w, uint32_t *scratch) {
+    uint32_t *P = X, *N = scratch;
+    memset(P, 0, (size_t)len * 4);
+    memset(N, 0, (size_t)len * 4);
+    for (int64_t i = 0; i < n; ++i)
+        memcpy((xn[i] ? N : P) + (size_t)i * w, x + (size_t)i * l, (size_t)l * 4);
+    if (cmp_n(P, N, len) >= 0) {
+        sub_n(P, P, N, len);
+        return 0;
+    }
+    sub_n(P, N, P, len);
+    return 1;
+}
+
+/*
+ * Full product by Kronecker substitution and Karatsuba.  Same arguments and
+ * results as orc_polymul.  Returns 0, -1 (bad arguments), -2 (a
+ * coefficient does not fit lc limbs, or the packed product is not
+ * consistent), -3 (out of memory).
+ */
+int orc_polymul_kron(int64_t na, int32_t la, const uint32_t *a, const uint8_t *an,
+                     int64_t nb, int32_t lb, const uint32_t *b, const uint8_t *bn,
+                     int32_t lc, uint32_t *c, uint8_t *cn, int32_t nthreads) {
+    if (na < 1 || nb < 1 || la < 1 || lb < 1 || lc < 1 || !a || !b || !an || !bn || !c || !cn) return -1;
+    const int32_t w = lc + 1;                  /* slot: s = 32 w bits */
+    if (la > w || lb > w) return -1;
+    const int64_t nmax = na > nb ? na : nb, nc = na + nb - 1;
+    int64_t len = nmax * w + 2;                /* limbs of each packed operand */
+    len += len & 1;
+    uint32_t *A = (uint32_t *)malloc((size_t)len * 4), *B = (uint32_t *)malloc((size_t)len * 4);
+    uint32_t *S = (uint32_t *)malloc((size_t)len * 4), *R = (uint32_t *)malloc((size_t)(2 * len) * 4);
+    int st = -3;
+    if (!A || !B || !S || !R) goto done;
+    const int sa = pack_signed(A, len, a, an, na, la, w, S);
+    const int sbg = pack_signed(B, len, b, bn, nb, lb, w, S);
+    st = orc_kara_mul(len, A, B, R, nthreads);
+    if (st) goto done;
+    const int64_t rlen = 2 * len;
+    if (sa ^ sbg) {                            /* two's complement of the product */
+        uint64_t cy = 1;
+        for (int64_t k = 0; k < rlen; ++k) {
+            uint64_t v = (uint64_t)(uint32_t)~R[k] + cy;
+            R[k] = (uint32_t)v;
+            cy = v >> 32;
+        }
+    }
+    /* read the signed slots back, lowest first */
+    uint32_t borrow = 0;
+    for (int64_t k = 0; k < nc; ++k) {
+        uint32_t *slot = R + (size_t)k * w;
+        uint64_t cy = borrow;                  /* t = slot + borrow, in place */
+        for (int32_t q = 0; q < w && cy; ++q) {
+            uint64_t v = (uint64_t)slot[q] + cy;
+            slot[q] = (uint32_t)v;
+            cy = v >> 32;
+        }
+        /* cy = 1 only when slot was all ones and borrow 1: t = 2^s, i.e. 0 with a borrow out */
+        const int negative = cy || (slot[w - 1] >> 31);
+        borrow = negative ? 1u : 0u;
+        uint32_t *out = c + (size_t)k * lc;
+        int nz = 0;
+        if (negative && !cy) {                 /* |c_k| = 2^s - t */
+            uint64_t b2 = 1;
+            for (int32_t q = 0; q < w; ++q) {
+                uint64_t v = (uint64_t)(uint32_t)~slot[q] + b2;
+                slot[q] = (uint32_t)v;
+                b2 = v >> 32;
+            }
+        } else if (cy) {
+            memset(slot, 0, (size_t)w * 4);
+        }
+        if (slot[w - 1] != 0) { st = -2; goto done; }  /* beyond lc limbs */
+        for (int32_t q = 0; q < lc; ++q) { out[q] = slot[q]; nz |= slot[q] != 0; }
+        cn[k] = (uint8_t)(nz && negative);
+    }
+    /* the rest of the product must be the sign extension the borrow cancels */
+    for (int64_t q = nc * w; q < rlen; ++q)
+        if (R[q] != (borrow ? 0xffffffffu : 0u)) { st = -2; goto done; }
+    st = 0;
+done:
+    free(A); free(B); free(S); free(R);
+    return st;
+}

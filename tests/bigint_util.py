@@ -92,3 +92,27 @@ def terms(k: int, na: int, nb: int) -> int:
 # Independent 61-bit primes (none is an NTT prime of the library: those are
 # below 2^30) for Schwartz-Zippel checks of whole outputs.
 CHECK_PRIMES = [(1 << 61) - 1, 2305843009213693921, 2305843009213693907]
+
+
+GOLDEN_DIR = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)),
+                                        "golden")
+
+
+def full_output_digest(c, cn):
+    """SHA-256 of a whole product as tests/golden/make_full_digests.py
+    writes it: little-endian uint32 limb rows, then the sign bytes."""
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(c).astype("<u4").tobytes() +
+                          np.ascontiguousarray(cn).tobytes()).hexdigest()
+
+
+def stored_full_digest(name):
+    """The oracle's full-size digest of workload `name`
+    (tests/golden/full_size_digests.json), or None."""
+    import json
+    import os
+    path = os.path.join(GOLDEN_DIR, "full_size_digests.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(name)
+    return rec["sha256"] if rec else None

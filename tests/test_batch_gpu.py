@@ -28,12 +28,25 @@ def _cuda():
     build.build()
 
 
-def test_full_batch_workload():
+@pytest.mark.parametrize("chosen_form", [False, True], ids=["planner", "costmodel_graph"])
+def test_full_batch_workload(chosen_form):
+    """chosen_form: the flags bench.py times the batch with (the learned
+    dispatch with the committed model and sweep table, graph replay)."""
     shapes = W.batch_shapes(seed=3, count=4096)
     ops = W.batch_operands(shapes, seed=3)
-    plan = ipm.Plan([(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes], flags=ipm.IPM_SYNC)
+    flags = ipm.IPM_SYNC
+    if chosen_form:
+        from paper_1612_05778_gb300 import costmodel as cmod
+        cmod.install(points=cmod.load_sweep()["points"])
+        flags |= ipm.IPM_COSTMODEL | ipm.IPM_GRAPH
+    plan = ipm.Plan([(s.na, s.nb, s.bits_a, s.bits_b) for s in shapes], flags=flags)
     dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
-    outs = plan.mul_batched(dev)
+    outs = [plan.empty_output(i) for i in range(len(shapes))]
+    for _ in range(2 if chosen_form else 1):  # a graph is recorded by the first call, replayed by the second
+        for c, cn in outs:
+            c.fill_(-1)
+            cn.fill_(7)
+        plan.mul_batched(dev, outs)
     torch.cuda.synchronize()
     host = [ipm.to_host(c, cn) for c, cn in outs]
     rng = np.random.default_rng(31)
@@ -60,3 +73,6 @@ def test_full_batch_workload():
             want = oracle.coeffs(ks, a, b, s.lc)
             assert np.array_equal(c[ks], want[0]) and np.array_equal(cn[ks], want[1]), i
     plan.close()
+    if chosen_form:
+        ipm.set_cost_model(None)
+        ipm.set_tuned([])

@@ -49,9 +49,39 @@ def test_stage_bits(logL, want):
     assert sum(want) == logL
 
 
-@pytest.mark.parametrize("workload", ["batch", "taylor", "paper_table"])
+@pytest.mark.parametrize("workload", ["taylor", "paper_table"])
 def test_single_gpu_workloads_leave_other_ranks_idle(workload, monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("LOCAL_RANK", "1")
     assert bench.main(["--workload", workload, "--gpus", "2"]) == 0
+
+
+def test_schedule_bytes_are_eight_slabs_plus_io(large_dense_info):
+    """The method's three-pass schedule moves in + out + 8R, R = r Y K 4
+    bytes (K1 writes 2R, K2 reads 2R and writes 2R, K3 reads 2R); this
+    implementation moves in + out + 12R (both x halves of both operands
+    leave the first pass)."""
+    I = large_dense_info
+    R = I["r"] * I["Y"] * I["K"] * 4
+    inp, out = bench.io_bytes(I)
+    s = bench.schedule_bytes(I)
+    a = bench.algorithmic_bytes(I)
+    assert s == [inp + 2 * R, 4 * R, 2 * R + out]
+    assert sum(s) == inp + out + 8 * R and sum(a) == inp + out + 12 * R
+    assert abs(sum(s) - 0.906e9) / 0.906e9 < 0.01  # 0.91 GB for d = 32768, 4096-bit
+
+
+def test_both_arms_print_the_same_config():
+    """The reference arm (the oracle, on a bounded sample) and our arm build
+    `config` from the same function, so the driver sees one workload."""
+    import io
+    import json
+    from contextlib import redirect_stdout
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        assert bench.main(["--impl", "reference", "--workload", "small_dense", "--steps", "1", "--warmup", "0"]) == 0
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    name, sh, _, _ = bench.workload("small_dense")
+    assert line["config"] == bench.workload_config(name, sh)
+    assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"

@@ -217,3 +217,85 @@ def test_small_dense_full_size_kronecker():
     c = oracle.polymul(a, b, sh.lc)
     want = kronecker_product(to_ints(*a), to_ints(*b), 32 * sh.lc + 2)
     assert to_ints(*c) == want
+
+
+# ---------------------------------------------------------------------------
+# The full-output oracle at large sizes: Kronecker substitution with the
+# oracle's own Karatsuba (oracle.polymul_kron).  Pinned to Python's
+# independent integers (the integer product alone, across the schoolbook
+# threshold, odd and uneven splits, carries through all-ones limbs) and to
+# the schoolbook definition on whole outputs (signs, zeros, unbalanced
+# degrees, extreme magnitudes, cancellation).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("limbs", [1, 2, 63, 64, 65, 127, 129, 300, 1001, 4096])
+@pytest.mark.parametrize("threads", [1, 5])
+def test_karatsuba_matches_python_integers(limbs, threads):
+    rng = np.random.default_rng(limbs * 7 + threads)
+    for kind in ("random", "ones", "lopsided"):
+        if kind == "random":
+            x = int.from_bytes(rng.bytes(4 * limbs), "little")
+            y = int.from_bytes(rng.bytes(4 * limbs), "little")
+        elif kind == "ones":
+            x = y = (1 << (32 * limbs)) - 1
+        else:  # one operand much shorter: the upper halves are zero
+            x = int.from_bytes(rng.bytes(4 * limbs), "little")
+            y = int.from_bytes(rng.bytes(4), "little") | 1
+        assert oracle.kara_mul(x, y, threads=threads) == x * y
+
+
+@pytest.mark.parametrize("na,nb,ba,bb", [
+    (1, 1, 1, 1), (2, 1, 4096, 5), (5, 3, 70, 33), (64, 64, 1, 1), (300, 257, 255, 255),
+    (1024, 1024, 255, 255), (700, 1500, 1000, 64), (3, 2000, 2048, 32), (129, 128, 4096, 4096)])
+def test_kronecker_karatsuba_matches_schoolbook(na, nb, ba, bb):
+    rng = np.random.default_rng(na * 31 + nb)
+    a = W.random_poly(rng, na, ba)
+    b = W.random_poly(rng, nb, bb)
+    lc = _lc(na, nb, ba, bb)
+    want = oracle.polymul(a, b, lc)
+    got = oracle.polymul_kron(a, b, lc, threads=3)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+def test_kronecker_karatsuba_extremes_and_cancellation():
+    # every magnitude 2^bits - 1 with all signs equal: the largest |c_k|
+    for neg in (False, True):
+        a = W.constant_poly(500, 300, negative=neg)
+        b = W.constant_poly(400, 300)
+        lc = _lc(500, 400, 300, 300)
+        want = oracle.polymul(a, b, lc)
+        got = oracle.polymul_kron(a, b, lc)
+        assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    # (y - 1)(y + 1) = y^2 - 1 with huge equal magnitudes: c_1 cancels to +0
+    big = (1 << 2000) - 12345
+    a = from_ints([-big, big], 63)
+    b = from_ints([big, big], 63)
+    got = oracle.polymul_kron(a, b, _lc(2, 2, 2016, 2016))
+    assert to_ints(*got) == [-big * big, 0, big * big] and got[1][1] == 0
+    # zero polynomials
+    z = from_ints([0] * 17, 4)
+    got = oracle.polymul_kron(z, W.random_poly(np.random.default_rng(3), 9, 100), _lc(17, 9, 128, 100))
+    assert not got[0].any() and not got[1].any()
+
+
+def test_kronecker_karatsuba_rejects_a_too_small_output():
+    a = W.constant_poly(64, 256)
+    with pytest.raises(RuntimeError):
+        oracle.polymul_kron(a, a, 8)  # |c_k| needs 17 limbs
+
+
+def test_full_size_digests_were_written_by_the_oracle():
+    """The stored full-size digests (tests/golden/make_full_digests.py) name
+    the same seeded inputs the workloads module generates today."""
+    path = os.path.join(GOLDEN, "full_size_digests.json")
+    if not os.path.exists(path):
+        pytest.skip("no full-size digests")
+    store = json.load(open(path))
+    makers = {"large_dense": lambda: W.large_dense(seed=1), "huge_dense": lambda: W.huge_dense(seed=2),
+              "huge_mixed": lambda: W.huge_mixed(seed=2)}
+    for name, rec in store.items():
+        sh, a, b = makers[name]()
+        assert rec["nc"] == sh.nc and rec["lc"] == sh.lc
+        assert rec["inputs_sha256"] == hashlib.sha256(a[0].tobytes() + a[1].tobytes() + b[0].tobytes() +
+                                                      b[1].tobytes()).hexdigest()
+        assert "oracle.polymul_kron" in rec["written_by"]

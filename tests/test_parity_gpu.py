@@ -1,12 +1,16 @@
 """GPU parity: the CUDA path against the CPU oracle, bit-exact on every limb
 and sign (integer work: exact equality is the only tolerance).
 
-Small and mid sizes compare whole outputs with the oracle.  The large dense
-workload (two degree-32767 polynomials with 4096-bit coefficients, the
-configuration bench.py times, same plan and launches) is checked on sampled
+Small and mid sizes compare whole outputs with the oracle.  The full-size
+workloads (two degree-32767 polynomials with 4096-bit coefficients; two of
+degree 262143 with 1024-bit or mixed 64/2048-bit coefficients) are compared
+on every limb and sign through the SHA-256 digest of the oracle's whole
+product (Kronecker substitution with the oracle's own Karatsuba,
+tests/golden/make_full_digests.py), with both the analytic planner's plan
+and the plan bench.py times (the learned dispatch), and also on sampled
 coefficients computed one by one by the oracle, on the exact identities
 C(1) = A(1)B(1) and C(-1) = A(-1)B(-1), and on evaluation modulo three
-independent 61-bit primes; its all-(2^4096-1) variant is checked in full
+independent 61-bit primes; the all-(2^4096-1) variant is checked in full
 against the closed form c_k = terms(k) (2^4096-1)^2.
 """
 import hashlib
@@ -19,7 +23,8 @@ import pytest
 import oracle
 import paper_1612_05778_gb300 as ipm
 import workloads as W
-from bigint_util import CHECK_PRIMES, eval_at, from_ints, terms, to_ints
+from bigint_util import (CHECK_PRIMES, eval_at, from_ints, full_output_digest, stored_full_digest, terms,
+                         to_ints)
 
 pytestmark = pytest.mark.gpu
 
@@ -289,10 +294,39 @@ def _whole_output_identities(a, b, c):
         assert oracle.eval_mod(c, t, q) == oracle.eval_mod(a, t, q) * oracle.eval_mod(b, t, q) % q
 
 
+def assert_full_digest(name, got):
+    """Every limb and sign of a full-size product against the oracle's."""
+    want = stored_full_digest(name)
+    assert want is not None, "tests/golden/full_size_digests.json lacks " + name
+    assert full_output_digest(*got) == want
+
+
+def chosen_plan_params(sh):
+    """The parameters the learned dispatch (committed model and sweep
+    table, as bench.py installs them) picks for this shape."""
+    from paper_1612_05778_gb300 import costmodel as cmod
+    cmod.install(points=cmod.load_sweep()["points"])
+    prm, _ = ipm.dispatch(sh.na, sh.nb, sh.bits_a, sh.bits_b)
+    ipm.set_cost_model(None)
+    ipm.set_tuned([])
+    return {k: v for k, v in prm.items() if v}
+
+
+@pytest.mark.parametrize("name,make", [("large_dense", lambda: W.large_dense(seed=1)),
+                                       ("huge_dense", lambda: W.huge_dense(seed=2)),
+                                       ("huge_mixed", lambda: W.huge_mixed(seed=2))])
+def test_full_size_every_limb_with_the_benchmarked_plan(name, make):
+    sh, a, b = make()
+    got, info = gpu_mul(a, b, sh.bits_a, sh.bits_b, **chosen_plan_params(sh))
+    assert info["lc"] == sh.lc
+    assert_full_digest(name, got)
+
+
 def test_large_dense_full_size():
     sh, a, b = W.large_dense(seed=1)
     got, info = gpu_mul(a, b, sh.bits_a, sh.bits_b)
     assert info["lc"] == sh.lc == 257
+    assert_full_digest("large_dense", got)
     # sampled coefficients, each computed by the oracle on its own
     nc = sh.nc
     ks = [0, 1, 2, 31, 4095, 16383, 32766, 32767, 32768, 49151, nc - 2, nc - 1]
@@ -321,20 +355,22 @@ def _sampled_and_identities(sh, a, b, extra_ks=()):
     want = oracle.coeffs(ks, a, b, sh.lc)
     assert_same((got[0][ks], got[1][ks]), want)
     _whole_output_identities(a, b, got)
-    return info
+    return info, got
 
 
 def test_huge_dense_full_size():
     """Two degree-262143 polynomials, 1024-bit coefficients (seed 2)."""
     sh, a, b = W.huge_dense(seed=2)
-    info = _sampled_and_identities(sh, a, b)
+    info, got = _sampled_and_identities(sh, a, b)
     assert info["Y"] == 1 << 19
+    assert_full_digest("huge_dense", got)
 
 
 def test_huge_mixed_full_size():
     """Half the positions < 2^64, the rest < 2^2048, random positions."""
     sh, a, b = W.huge_mixed(seed=2)
-    _sampled_and_identities(sh, a, b)
+    _, got = _sampled_and_identities(sh, a, b)
+    assert_full_digest("huge_mixed", got)
 
 
 def test_batched_with_split_middle_transform():

@@ -18,7 +18,7 @@ import pytest
 import oracle
 import paper_1612_05778_gb300 as ipm
 import workloads as W
-from bigint_util import CHECK_PRIMES, eval_at, to_ints
+from bigint_util import CHECK_PRIMES, eval_at, full_output_digest, stored_full_digest, to_ints
 
 pytestmark = pytest.mark.gpu
 
@@ -141,3 +141,6 @@ def test_tensor_stages_full_size(which):
     _identities(a, b, got)
     ref, _ = gpu_mul(a, b, sh.bits_a, sh.bits_b, 0)
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    # every limb and sign against the oracle's whole product
+    want = stored_full_digest(which)
+    assert want is not None and full_output_digest(*got) == want
