@@ -33,6 +33,17 @@ constexpr int OUTER_TILE_WORDS = 8192;  // outer-pass tile: Y1b rows x W words
 // slices (ntt_stages.cuh, stage_tc16), 1024 words each.
 constexpr int TC_FRAG_WORDS = 2048;
 
+// Middle-pass tile rows (passes.cuh, mid_tile): for slices of S < 32
+// columns, one empty row after every 2^pl rows, 2^pl the radix of the last
+// stage of the length-2^logY1a column transform (the register stages split
+// log2 L into ceil(log2 L / 4) stages as evenly as possible, the last one
+// smallest); 0 (odd pitch S + 1 instead) for S >= 32.
+__host__ __device__ inline int mid_pad_log(int logY1a, int S) {
+    if (S >= 32 || logY1a < 1) return 0;
+    const int nst = (logY1a + 3) / 4;
+    return logY1a / nst;
+}
+
 // Device error word bits.
 constexpr int ERRBIT_BOUND = 1;      // an input coefficient >= 2^bits
 constexpr int ERRBIT_INTERNAL = 2;   // recombination top limb not a sign word

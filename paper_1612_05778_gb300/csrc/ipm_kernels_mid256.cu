@@ -48,12 +48,7 @@ int launch_batch_middle256(const BatchLaunch &bl, void *stream) {
 }
 
 // A group may take the 256-thread middle when its largest tile fits two
-// blocks per SM and the tile fill's warp-to-row map works with 8 warps:
-// rows S apart need S | 8 when 1 < S < 32 and the column has >= 32 rows.
-bool mid256_ok(const KParams &kp, size_t smem_mid) {
-    if (smem_mid > MID256_SMEM_MAX) return false;
-    const bool rot = kp.S < 32 && kp.S > 1 && kp.Y1a >= 32;
-    return !rot || (8 % kp.S) == 0;
-}
+// blocks per SM (the tile function works with any block size).
+bool mid256_ok(const KParams &, size_t smem_mid) { return smem_mid <= MID256_SMEM_MAX; }
 
 }  // namespace ipm

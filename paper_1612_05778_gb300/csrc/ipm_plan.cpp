@@ -164,11 +164,14 @@ size_t inv_smem(int64_t Y2, int K, int r, int lc) {
     size_t tables = (size_t)r * (2 * (size_t)Y2 + (size_t)K) * 8;  // per prime: row / x / y twiddles
     return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources + tables;
 }
-// tiles of A and B, plus (tables) one omega table pair per stage: Y1
-// entries for the first, and fewer than Y1 / 7 for all later ones together
-// (the first stage has radix >= 8 when there are several)
+// tiles of A and B (for S < 32 rows of S words with one empty row after
+// every 2^pl, else rows at pitch S + 1), plus (tables) one omega table pair
+// per stage: Y1 entries for the first, and fewer than Y1 / 7 for all later
+// ones together (the first stage has radix >= 8 when there are several)
 size_t mid_smem(int64_t Y1, int S, bool tables) {
-    return ((size_t)2 * Y1 * (S + 1) + 16) * 4 + (tables ? (size_t)2 * (Y1 + Y1 / 4 + 16) * 8 : 0);
+    const int pl = mid_pad_log(ilog2((uint64_t)Y1), S);
+    const size_t tile = pl ? (size_t)(Y1 + (Y1 >> pl)) * S : (size_t)Y1 * (S + 1);
+    return (2 * tile + 16) * 4 + (tables ? (size_t)2 * (Y1 + Y1 / 4 + 16) * 8 : 0);
 }
 // outer pass: Y1b rows x W consecutive words of one operand (W a power of
 // two >= 4, about OUTER_TILE_WORDS words per tile)
@@ -180,7 +183,8 @@ size_t outer_smem(int64_t Y1b, int64_t W) { return (size_t)Y1b * (size_t)W * 4; 
 // Tile shapes: Y2 rows per forward/inverse tile, S columns per middle tile
 // (Y1 = Y / Y2 is the middle pass's column length).  Hard limit: every pass
 // fits one block's shared memory.  Preferences, in order: middle slices of
-// at least 8 columns (32-byte DRAM sectors), an inverse tile small enough
+// at least 4 columns (one 16-byte copy per row; 8 columns fill a 32-byte
+// DRAM sector and are preferred slightly), an inverse tile small enough
 // for two CTAs per SM, a forward tile small enough for three, no split of
 // the middle transform (a split costs an extra pass over the data), and Y2
 // close to max(32, Y / 2048).  When Y1 is long, the middle transform may be
@@ -224,7 +228,8 @@ bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force
             if (S == 0) continue;
             const int64_t S2 = Y1b > 1 ? outer_width(Y1a, K, Y1b) : 0;
             if (Y1b > 1 && outer_smem(Y1b, S2) > SMEM_MID_MAX) continue;
-            const double score = (S >= 8 || S == 2 * K ? 0 : 8) + (iv <= SMEM_INV_2PERSM ? 0 : 4) +
+            // slices narrower than 4 words fill less than a 16-byte copy per row
+            const double score = (S >= 8 || S == 2 * K ? 0 : S >= 4 ? 1 : 8) + (iv <= SMEM_INV_2PERSM ? 0 : 4) +
                                  (fw <= SMEM_FWD_3PERSM ? 0 : 2) + (tab ? 0 : 1) + (Y1b > 1 ? 3 : 0) +
                                  0.1 * std::abs(ilog2((uint64_t)Y2) - ilog2((uint64_t)target));
             if (!found || score < best) {

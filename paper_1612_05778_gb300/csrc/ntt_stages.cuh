@@ -102,22 +102,85 @@ __device__ __forceinline__ void dft_dif_hz(uint32_t (&x)[R], const Roots<R> &rt,
     }
 }
 
-// In-register inverse DFT (roots omega_R^{-j}), bit-reversed in, natural out.
+// dft_dif followed by the stage twiddle of every output m >= 1, with the
+// twiddle folded into the last butterfly level: the unreduced sum and
+// difference of a unit butterfly (x + y and x - y + 2p, both < 4p < 2^32)
+// go straight into Shoup's multiplication, which accepts any 32-bit input
+// and returns [0, 2p) -- two reductions fewer per twiddled output.
+// HZ: the upper half of the inputs is zero (as dft_dif_hz).
+template <int R, bool HZ>
+__device__ __forceinline__ void dft_dif_tw(uint32_t (&x)[R], const Roots<R> &rt, const uint2 (&w)[R], uint32_t p,
+                                           uint32_t p2) {
+    if constexpr (R == 2) {
+        if (HZ) {
+            x[1] = shoup(x[0], w[1], p);  // (x0, 0) -> (x0, x0 w1)
+        } else {
+            const uint32_t s = x[0] + x[1], d = x[0] - x[1] + p2;
+            x[0] = red(s, p2);
+            x[1] = shoup(d, w[1], p);
+        }
+    } else {
+        int h0 = R / 2;
+        if (HZ) {
+            x[R / 2] = x[0];
+#pragma unroll
+            for (int k = 1; k < R / 2; ++k) x[k + R / 2] = shoup(x[k], rt.w[k], p);
+            h0 = R / 4;
+        }
+#pragma unroll
+        for (int h = R / 2; h >= 2; h >>= 1) {
+            if (h > h0) continue;
+#pragma unroll
+            for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+                for (int k = 0; k < h; ++k) {
+                    if (k == 0)
+                        bf_unit(x[b], x[b + h], p2);
+                    else
+                        bf_dif(x[b + k], x[b + k + h], rt.w[k * (R / (2 * h))], p, p2);
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < R; b += 2) {
+            const uint32_t s = x[b] + x[b + 1], d = x[b] - x[b + 1] + p2;
+            x[b] = b == 0 ? red(s, p2) : shoup(s, w[b], p);
+            x[b + 1] = shoup(d, w[b + 1], p);
+        }
+    }
+}
+
+// In-register inverse DFT (roots omega_R^{-j}), bit-reversed in, natural
+// out, inputs and outputs in [0, 2p).  Harvey's lazy Cooley-Tukey
+// butterflies (D. Harvey, J. Symb. Comp. 60, 2014): between levels the
+// values may reach [0, 4p); a butterfly brings only its x input back to
+// [0, 2p) (the Shoup product of y accepts any 32-bit input), then forms
+// x + t and x - t + 2p without reducing them.  The first level's inputs are
+// already in [0, 2p) and its twiddles are 1, so it needs no reduction.
 template <int R>
 __device__ __forceinline__ void dft_dit(uint32_t (&x)[R], const Roots<R> &rt, uint32_t p, uint32_t p2) {
 #pragma unroll
-    for (int h = 1; h < R; h <<= 1) {
+    for (int b = 0; b < R; b += 2) {
+        const uint32_t s = x[b] + x[b + 1], d = x[b] - x[b + 1] + p2;
+        x[b] = s;
+        x[b + 1] = d;
+    }
+#pragma unroll
+    for (int h = 2; h < R; h <<= 1) {
 #pragma unroll
         for (int b = 0; b < R; b += 2 * h) {
 #pragma unroll
             for (int k = 0; k < h; ++k) {
-                if (k == 0)
-                    bf_unit(x[b], x[b + h], p2);
-                else
-                    bf_dit(x[b + k], x[b + k + h], rt.w[k * (R / (2 * h))], p, p2);
+                const uint32_t xa = red(x[b + k], p2);
+                const uint32_t t = k == 0 ? red(x[b + k + h], p2)
+                                          : shoup(x[b + k + h], rt.w[k * (R / (2 * h))], p);
+                x[b + k] = xa + t;
+                x[b + k + h] = xa - t + p2;
             }
         }
     }
+#pragma unroll
+    for (int m = 0; m < R; ++m) x[m] = red(x[m], p2);
 }
 
 struct TileMap {
@@ -127,7 +190,18 @@ struct TileMap {
     int ta, tb;  // strides of t % tm and t / tm
     int es;      // element stride
     int rot;     // log2 T for tiles of T < 32 transforms at row pitch T + 1, else 0 (see rotate_rows)
+    // Padded rows: 0, or log2 P for a tile that leaves one empty element
+    // slot after every P elements, so element n lives at slot n + n / P.
+    // With P the radix of the transform's last stage, the last stage's
+    // groups (P consecutive elements each, P apart) land on distinct banks
+    // even at a dense row pitch (P + 1 slots per P elements); every earlier
+    // stage's stride L' is a multiple of P, so its elements stay evenly
+    // spaced (L' + L'/P slots apart).
+    int pl = 0;
 };
+
+// Slot of element n in a padded tile (see TileMap::pl).
+__device__ __forceinline__ int padded(const TileMap &M, int n) { return M.pl ? n + (n >> M.pl) : n; }
 
 // With T < 32 transforms at row pitch T + 1, a warp's gathers touch 32 / T
 // rows; rows T apart land on disjoint banks ((T + 1) T j = 0 mod T, and the
@@ -185,7 +259,7 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
     const int total = M.T << (logL - LR);
     const int tsh = logT - logLc;
     const int lT = ilog2_if_pow2(M.T), ltm = ilog2_if_pow2(M.tm);
-    const int st = Lp * M.es;
+    const int st = padded(M, Lp) * M.es;
     const bool rot = M.rot && logLp >= 5;
     for (int g = threadIdx.x; g < total; g += blockDim.x) {
         int rest;
@@ -193,7 +267,7 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
         if (rot) rest = rotate_rows(rest, M.rot);
         const int n1 = rest & (Lp - 1);
         const int blk = rest >> logLp;
-        uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
+        uint32_t *base = tb + padded(M, (blk << logLc) + n1) * M.es;
         uint32_t x[R];
         if (Lp > 1) {
             // twiddles omega_Lc^{n1 k2} first: their latency hides behind the
@@ -201,16 +275,12 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
             const uint2 *wb = tw;
             const uint32_t step = (uint32_t)n1 << tsh;
             uint2 w[R];
+            w[0] = make_uint2(1u, 0u);  // unused: output 0 carries no twiddle
 #pragma unroll
             for (int m = 1; m < R; ++m) w[m] = tload<SM>(wb + step * (uint32_t)brev_c<R>(m));
 #pragma unroll
             for (int m = 0; m < (HZ ? R / 2 : R); ++m) x[m] = base[m * st];
-            if (HZ)
-                dft_dif_hz<R>(x, rt, p, p2);
-            else
-                dft_dif<R>(x, rt, p, p2);
-#pragma unroll
-            for (int m = 1; m < R; ++m) x[m] = shoup(x[m], w[m], p);
+            dft_dif_tw<R, HZ>(x, rt, w, p, p2);
         } else {  // last stage: every twiddle is 1
 #pragma unroll
             for (int m = 0; m < (HZ ? R / 2 : R); ++m) x[m] = base[m * st];
@@ -246,7 +316,7 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
     const int total = M.T << (logL - LR);
     const int tsh = logT - logLc;
     const int lT = ilog2_if_pow2(M.T), ltm = ilog2_if_pow2(M.tm);
-    const int st = Lp * M.es;
+    const int st = padded(M, Lp) * M.es;
     const bool rot = M.rot && logLp >= 5;
     for (int g = threadIdx.x; g < total; g += blockDim.x) {
         int rest;
@@ -254,7 +324,7 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
         if (rot) rest = rotate_rows(rest, M.rot);
         const int n1 = rest & (Lp - 1);
         const int blk = rest >> logLp;
-        uint32_t *base = tb + ((blk << logLc) + n1) * M.es;
+        uint32_t *base = tb + padded(M, (blk << logLc) + n1) * M.es;
         uint32_t x[R];
         if (Lp > 1) {
             const uint32_t step = (uint32_t)n1 << tsh;
@@ -339,7 +409,7 @@ __device__ __forceinline__ StageGroup stage_group(const TileMap &M, int lT, int 
     const int n1 = rest & ((1 << logLp) - 1);
     const int blk = rest >> logLp;
     StageGroup G;
-    G.base = tb + ((blk << logLc) + n1) * M.es;
+    G.base = tb + padded(M, (blk << logLc) + n1) * M.es;
     G.t = lT >= 0 ? (g & (M.T - 1)) : g % M.T;
     G.n0 = (blk << logLc) + n1;
     G.n1 = n1;
@@ -358,7 +428,7 @@ __device__ __forceinline__ void stage_tc16(const TileMap &M, int logL, int logLc
     const int total = M.T << (logL - 4);
     const int tsh = logT - logLc;
     const int lT = ilog2_if_pow2(M.T), ltm = ilog2_if_pow2(M.tm);
-    const int st = Lp * M.es;
+    const int st = padded(M, Lp) * M.es;
     const bool rot = M.rot && logLp >= 5;
     const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
     const uint4 *fr = reinterpret_cast<const uint4 *>(FWD ? tc.fwd : tc.inv) + 2 * lane;
@@ -533,8 +603,8 @@ __device__ __forceinline__ void stage_fused_pointwise(const TileMap &MA, const T
     const int lT = ilog2_if_pow2(MA.T), ltm = ilog2_if_pow2(MA.tm);
     for (int g = threadIdx.x; g < total; g += blockDim.x) {
         int blk;
-        uint32_t *ba = group_base(MA, lT, ltm, g, blk) + (blk << LR) * MA.es;
-        uint32_t *bb = group_base(MB, lT, ltm, g, blk) + (blk << LR) * MB.es;
+        uint32_t *ba = group_base(MA, lT, ltm, g, blk) + padded(MA, blk << LR) * MA.es;
+        uint32_t *bb = group_base(MB, lT, ltm, g, blk) + padded(MB, blk << LR) * MB.es;
         uint32_t xa[R], xb[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) {

@@ -245,7 +245,6 @@ template <bool SMTW, class TC>
 __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int pb, int t) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = P.S, logS = P.logS;
-    const int pitch = S + 1;  // odd pitch for conflict-free strided gathers
     const int twoK = 2 * P.K;
     const int Y1 = (int)P.Y1a;  // this tile's column length
     const PrimeConst &pc = P.pc[t];
@@ -261,24 +260,21 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
             logLc -= sbase + (i < sextra ? 1 : 0);
         }
     }
-    uint32_t *A = reinterpret_cast<uint32_t *>(SMTW ? (void *)(tab + tab_entries) : (void *)smem);  // [Y1a][pitch]
-    uint32_t *B = A + (size_t)Y1 * pitch + 16;          // [Y1][pitch], shifted 16 banks
+    // Tile layout.  S < 32 (a warp spans several rows): rows of S words at
+    // pitch S, one empty row after every R rows, R the radix of the column
+    // transform's last stage (TileMap::pl) -- every stage's warp accesses
+    // hit distinct banks and each row is 16-byte aligned for S >= 4.
+    // S >= 32: rows at the odd pitch S + 1.
+    const int pl = mid_pad_log(P.logY1a, S);
+    const int pitch = pl ? S : S + 1;
+    const int rows = pl ? Y1 + (Y1 >> pl) : Y1;
+    uint32_t *A = reinterpret_cast<uint32_t *>(SMTW ? (void *)(tab + tab_entries) : (void *)smem);
+    uint32_t *B = A + (size_t)rows * pitch + 16;  // shifted 16 banks
     const uint32_t p = pc.p, p2 = pc.p2;
     uint32_t *ZA = P.Z + (size_t)(t * 2 + 0) * (size_t)P.Y * twoK;
     const uint32_t *ZB = P.Z + (size_t)(t * 2 + 1) * (size_t)P.Y * twoK;
     const size_t base = ((size_t)pos * P.Y1 + (size_t)P.Y1a * pb) * twoK + (size_t)cs * S;
-    // Tile fill: thread -> (column c, first row r0), then rows r0 + k * rs.
-    // When S < 32 and the tile has whole 32-row blocks, the 32/S rows a warp
-    // touches are S apart (conflict-free at pitch S + 1, see rotate_rows):
-    // warp w, lane -> row 32 (w / S) + (w % S) + S (lane / S).  Rows grow by
-    // rs = blockDim / S per step (blockDim / 32 is a multiple of S).
-    const bool rot = S < 32 && S > 1 && Y1 >= 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c0 = threadIdx.x & (S - 1);
-    const int r0 = rot ? ((warp >> logS) << 5) + (warp & (S - 1)) + ((lane >> logS) << logS)
-                       : (int)(threadIdx.x >> logS);
-    const int rs = blockDim.x >> logS;
-    const bool simple = S <= 32;  // else: one thread walks elements e = tid + k blockDim
+    const TileMap tmp{A, S, S, 1, 0, pitch, 0, pl};
     if (SMTW) {  // stage i: omega_Lc^{+-e}, e < Lc = entries at stride Y1 / Lc (no split: Y1a = Y1),
                  // copied asynchronously with A's slice
         uint2 *f = tab;
@@ -294,33 +290,37 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
         }
     }
     // A's slice, then B's, as two asynchronous copy groups: B is still in
-    // flight while A is transformed
-    if (simple) {
-        for (int i1 = r0; i1 < Y1; i1 += rs) cp_async4(A + i1 * pitch + c0, ZA + base + (size_t)i1 * twoK + c0);
-        cp_async_commit();
-        for (int i1 = r0; i1 < Y1; i1 += rs) cp_async4(B + i1 * pitch + c0, ZB + base + (size_t)i1 * twoK + c0);
-        cp_async_commit();
-    } else {
-        for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
-            const int i1 = e >> logS, c = e & (S - 1);
-            cp_async4(A + i1 * pitch + c, ZA + base + (size_t)i1 * twoK + c);
+    // flight while A is transformed.  Rows of S words: 16-byte copies when
+    // both ends of every row are 16-byte aligned -- the dense padded layout
+    // (pitch S) with S a multiple of 4; row starts in global memory are
+    // multiples of 4 words from a 16-byte aligned slab -- else 4-byte
+    // copies (the odd pitch S + 1 of S >= 32 never allows 16-byte ones).
+    const bool copy16 = pl && S % 4 == 0;
+    auto fill = [&](uint32_t *T, const uint32_t *Z) {
+        if (copy16) {
+            const int logS4 = logS - 2;
+            for (int e = threadIdx.x; e < Y1 * (S >> 2); e += blockDim.x) {
+                const int i1 = e >> logS4, c4 = (e & ((S >> 2) - 1)) << 2;
+                cp_async16(T + (size_t)padded(tmp, i1) * pitch + c4, Z + base + (size_t)i1 * twoK + c4);
+            }
+        } else {
+            for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+                const int i1 = e >> logS, c = e & (S - 1);
+                cp_async4(T + (size_t)padded(tmp, i1) * pitch + c, Z + base + (size_t)i1 * twoK + c);
+            }
         }
         cp_async_commit();
-        for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
-            const int i1 = e >> logS, c = e & (S - 1);
-            cp_async4(B + i1 * pitch + c, ZB + base + (size_t)i1 * twoK + c);
-        }
-        cp_async_commit();
-    }
+    };
+    fill(A, ZA);
+    fill(B, ZB);
     cp_async_wait<1>();
     __syncthreads();
     // y step C (omega_Y1 = omega_Y^Y2) on the S columns of A and of B (B's
     // copies finish while A is transformed), the pointwise product in
     // Montgomery form A*B*2^-32 (the 2^32 is put back by the scale factor of
     // the inverse pass) and the inverse step C, written over A
-    const int rl = S < 32 && S > 1 ? logS : 0;
-    const TileMap am{A, S, S, 1, 0, pitch, rl};
-    const TileMap bm{B, S, S, 1, 0, pitch, rl};
+    const TileMap am{A, S, S, 1, 0, pitch, 0, pl};
+    const TileMap bm{B, S, S, 1, 0, pitch, 0, pl};
     // the last inverse stage stores its outputs, fully reduced, to the
     // workspace (rows i1, columns c of this slice)
     const MidStore out{ZA + base, twoK, p};
@@ -332,13 +332,9 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
         __syncthreads();
     }, out, tc);
     if (stored) return;
-    if (simple) {
-        for (int i1 = r0; i1 < Y1; i1 += rs) ZA[base + (size_t)i1 * twoK + c0] = red(A[i1 * pitch + c0], p);
-    } else {
-        for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
-            const int i1 = e >> logS, c = e & (S - 1);
-            ZA[base + (size_t)i1 * twoK + c] = red(A[i1 * pitch + c], p);
-        }
+    for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+        const int i1 = e >> logS, c = e & (S - 1);
+        ZA[base + (size_t)i1 * twoK + c] = red(A[(size_t)padded(tmp, i1) * pitch + c], p);
     }
 }
 
