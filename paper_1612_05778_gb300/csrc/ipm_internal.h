@@ -44,6 +44,22 @@ __host__ __device__ inline int mid_pad_log(int logY1a, int S) {
     return logY1a / nst;
 }
 
+// Offsets (uint2 entries) of the per-stage twiddle blocks of a compact
+// table for a length-2^logL transform: stage i at off[i], 2 (Lc_i + R_i)
+// entries; returns the total.
+__host__ __device__ inline int stage_blocks(int logL, int (&off)[8]) {
+    const int nst = (logL + 3) / 4;
+    const int base = nst ? logL / nst : 0, extra = nst ? logL % nst : 0;
+    int at = 0, logLc = logL;
+    for (int i = 0; i < nst; ++i) {
+        const int b = base + (i < extra ? 1 : 0);
+        off[i] = at;
+        at += 2 * ((1 << logLc) + (1 << b));
+        logLc -= b;
+    }
+    return at;
+}
+
 // Device error word bits.
 constexpr int ERRBIT_BOUND = 1;      // an input coefficient >= 2^bits
 constexpr int ERRBIT_INTERNAL = 2;   // recombination top limb not a sign word
@@ -160,6 +176,10 @@ TableLayout table_layout(int64_t Y, int64_t Y1, int32_t K);
 int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint8_t *an,
                    const uint32_t *b, const uint8_t *bn, void *stream);
 int launch_middle(const KParams &kp, size_t smem, void *stream);
+// SMs of the current device (cached per device), and the middle-pass tiles
+// of one product (column slices x Y2 x Y1b x primes).
+int sm_count();
+int middle_tiles(const KParams &kp);
 int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, void *stream);
 int launch_outer(const KParams &kp, size_t smem, bool forward, void *stream);
 // The launch sequence of the transform product kp describes (forward,

@@ -19,11 +19,13 @@
 //             c_i = sum_j c_{i,j} 2^{Mj} with full carry propagation and
 //             conversion to sign-magnitude.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <atomic>
 
 #include "ipm_internal.h"
 #include "modarith.cuh"
 #include "ntt_stages.cuh"
+#include "ipm_mid256.h"
 #include "passes.cuh"
 
 namespace ipm {
@@ -49,10 +51,10 @@ k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a, con
     fwd_tile<NoTc>(P, blockIdx.x, blockIdx.y, a, an, b, bn);
 }
 
+// persistent: one block per SM walks the tile list (passes.cuh, mid_tiles)
 template <bool SMTW>
 __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant__ KParams P) {
-    // blockIdx.y = pos * Y1b + pb
-    mid_tile<SMTW, NoTc>(P, blockIdx.x, blockIdx.y >> P.logY1b, blockIdx.y & (P.Y1b - 1), blockIdx.z);
+    mid_tiles<SMTW>(P);
 }
 
 // grid: x = pos * (Y1a 2K / W) + word block; y = 2t + op forward (both
@@ -127,6 +129,7 @@ int set_kernel_attributes() {
     set((const void *)kb_inverse<THREADS_INV>, SMEM_INV_MAX);
     set((const void *)kb_inverse<1024>, SMEM_INV_MAX);
     if (e == cudaSuccess && set_kernel_attributes_tc()) return -1;
+    if (e == cudaSuccess && set_kernel_attributes_mid256()) return -1;
     return e == cudaSuccess ? 0 : -1;
 }
 
@@ -182,9 +185,25 @@ int launch_outer(const KParams &kp, size_t smem, bool forward, void *stream) {
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+int sm_count() {
+    static int counts[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!counts[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        counts[dev] = n;
+    }
+    return counts[dev];
+}
+
+int middle_tiles(const KParams &kp) { return (int)(2 * kp.K / kp.S * kp.Y2 * kp.Y1b * kp.r); }
+
 int launch_middle(const KParams &kp, size_t smem, void *stream) {
     if (kp.tcfrag) return launch_middle_tc(kp, smem, stream);
-    dim3 grid((unsigned)(2 * kp.K / kp.S), (unsigned)(kp.Y2 * kp.Y1b), (unsigned)kp.r);
+    // tiles small enough for two blocks per SM run in 256-thread blocks
+    if (smem <= MID256_SMEM_MAX) return launch_middle256(kp, smem, stream);
+    const unsigned grid = (unsigned)std::min(middle_tiles(kp), sm_count());
     if (kp.mid_tables_in_smem)
         k_middle<true><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
     else

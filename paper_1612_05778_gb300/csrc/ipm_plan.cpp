@@ -165,13 +165,20 @@ size_t inv_smem(int64_t Y2, int K, int r, int lc) {
     return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources + tables;
 }
 // tiles of A and B (for S < 32 rows of S words with one empty row after
-// every 2^pl, else rows at pitch S + 1), plus (tables) one omega table pair
-// per stage: Y1 entries for the first, and fewer than Y1 / 7 for all later
-// ones together (the first stage has radix >= 8 when there are several)
+// every 2^pl, else rows at pitch S + 1), plus (tables) one twiddle block per
+// register stage of the length-Y1 transform, 2 (Lc_i + R_i) entries for the
+// stage's sub-block length Lc_i and radix R_i (ntt_stages.cuh,
+// stage_blocks; passes.cuh, mid_tile)
 size_t mid_smem(int64_t Y1, int S, bool tables) {
-    const int pl = mid_pad_log(ilog2((uint64_t)Y1), S);
+    const int logY1 = ilog2((uint64_t)Y1);
+    const int pl = mid_pad_log(logY1, S);
     const size_t tile = pl ? (size_t)(Y1 + (Y1 >> pl)) * S : (size_t)Y1 * (S + 1);
-    return (2 * tile + 16) * 4 + (tables ? (size_t)2 * (Y1 + Y1 / 4 + 16) * 8 : 0);
+    size_t tab = 0;
+    if (tables) {
+        int off[8];
+        tab = (size_t)stage_blocks(logY1, off);
+    }
+    return (2 * tile + 16) * 4 + tab * 8;
 }
 // outer pass: Y1b rows x W consecutive words of one operand (W a power of
 // two >= 4, about OUTER_TILE_WORDS words per tile)

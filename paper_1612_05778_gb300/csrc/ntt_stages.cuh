@@ -29,21 +29,33 @@ struct Roots {
     uint2 w[R / 2 > 0 ? R / 2 : 1];  // omega_R^{+-j}, j < R/2
 };
 
-// Twiddle-table read: SM = the table lives in shared memory, else in global
-// memory (read through the non-coherent cache).
-template <bool SM>
+// Where a stage's twiddles come from (the SM template argument of the
+// stage functions):
+//   TW_GLOBAL (0): omega_T^e, e < T, in global memory (non-coherent cache);
+//   TW_SHARED (1): the same table in shared memory;
+//   TW_STAGE  (2): a per-stage block in shared memory for a stage of
+//     sub-block length Lc = R L': entry m L' + n1 holds the twiddle
+//     omega_Lc^{n1 brev(m)} of output (forward) or input (inverse) m of
+//     group n1, and entries Lc .. Lc + R/2 - 1 the roots omega_R^j.  A
+//     warp's groups have consecutive n1, so its twiddle reads are
+//     consecutive entries (no bank conflicts) at addresses that need no
+//     multiplication; logT passes log2 Lc.
+constexpr int TW_GLOBAL = 0, TW_SHARED = 1, TW_STAGE = 2;
+
+template <int SM>
 __device__ __forceinline__ uint2 tload(const uint2 *p) {
-    if constexpr (SM)
+    if constexpr (SM != TW_GLOBAL)
         return *p;
     else
         return __ldg(p);
 }
 
-template <int R, bool SM>
+template <int R, int SM>
 __device__ __forceinline__ void load_roots(Roots<R> &rt, const uint2 *__restrict__ tab, int logT) {
     constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
 #pragma unroll
-    for (int j = 0; j < R / 2; ++j) rt.w[j] = tload<SM>(tab + ((uint32_t)j << (logT - LR)));
+    for (int j = 0; j < R / 2; ++j)
+        rt.w[j] = SM == TW_STAGE ? tab[(1u << logT) + j] : tload<SM>(tab + ((uint32_t)j << (logT - LR)));
 }
 
 template <int R>
@@ -247,7 +259,7 @@ struct TileOut {
     __device__ __forceinline__ void put(uint32_t *a, int, int, uint32_t v) const { *a = v; }
 };
 
-template <int R, bool SM, bool HZ = false, class Out = TileOut>
+template <int R, int SM, bool HZ = false, class Out = TileOut>
 __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
                                           uint32_t p2, const Out &out = Out()) {
@@ -277,7 +289,8 @@ __device__ __forceinline__ void stage_dif(const TileMap &M, int logL, int logLc,
             uint2 w[R];
             w[0] = make_uint2(1u, 0u);  // unused: output 0 carries no twiddle
 #pragma unroll
-            for (int m = 1; m < R; ++m) w[m] = tload<SM>(wb + step * (uint32_t)brev_c<R>(m));
+            for (int m = 1; m < R; ++m)
+                w[m] = SM == TW_STAGE ? wb[m * Lp + n1] : tload<SM>(wb + step * (uint32_t)brev_c<R>(m));
 #pragma unroll
             for (int m = 0; m < (HZ ? R / 2 : R); ++m) x[m] = base[m * st];
             dft_dif_tw<R, HZ>(x, rt, w, p, p2);
@@ -304,7 +317,7 @@ struct TileIn {
     __device__ __forceinline__ uint32_t get(const uint32_t *a, int, int) const { return *a; }
 };
 
-template <int R, bool SM, class In = TileIn, class Out = TileOut>
+template <int R, int SM, class In = TileIn, class Out = TileOut>
 __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
                                           uint32_t p2, const In &in = In(), const Out &out = Out()) {
@@ -330,7 +343,8 @@ __device__ __forceinline__ void stage_dit(const TileMap &M, int logL, int logLc,
             const uint32_t step = (uint32_t)n1 << tsh;
             uint2 w[R];
 #pragma unroll
-            for (int m = 1; m < R; ++m) w[m] = tload<SM>(tw + step * (uint32_t)brev_c<R>(m));
+            for (int m = 1; m < R; ++m)
+                w[m] = SM == TW_STAGE ? tw[m * Lp + n1] : tload<SM>(tw + step * (uint32_t)brev_c<R>(m));
 #pragma unroll
             for (int m = 0; m < R; ++m) x[m] = base[m * st];
 #pragma unroll
@@ -419,7 +433,7 @@ __device__ __forceinline__ StageGroup stage_group(const TileMap &M, int lT, int 
 // One radix-16 stage (the same groups, twiddles and output order as
 // stage_dif<16> when FWD, stage_dit<16> otherwise) on the tensor cores.
 // HZ: inputs 8..15 of every group are zero (forward only): one K-chunk.
-template <bool FWD, bool HZ, bool SM, class In = TileIn, class Out = TileOut>
+template <bool FWD, bool HZ, int SM, class In = TileIn, class Out = TileOut>
 __device__ __forceinline__ void stage_tc16(const TileMap &M, int logL, int logLc, const uint2 *__restrict__ tw,
                                            int logT, uint32_t p, const TcOn &tc, const In &in = In(),
                                            const Out &out = Out()) {
@@ -443,7 +457,9 @@ __device__ __forceinline__ void stage_tc16(const TileMap &M, int logL, int logLc
                 if (FWD)
                     b[i] = G.base[k * st];
                 else if (Lp > 1)  // inverse: the twiddle omega_Lc^{-n1 brev(k)} first
-                    b[i] = shoup(G.base[k * st], tload<SM>(tw + step * bitrev((uint32_t)k, 4)), p);
+                    b[i] = shoup(G.base[k * st],
+                                 SM == TW_STAGE ? tw[k * Lp + G.n1] : tload<SM>(tw + step * bitrev((uint32_t)k, 4)),
+                                 p);
                 else
                     b[i] = in.get(G.base + k * st, G.t, G.n0 + k);
             }
@@ -467,7 +483,9 @@ __device__ __forceinline__ void stage_tc16(const TileMap &M, int logL, int logLc
                 const uint32_t lo = d[0][e] + (d[1][e] << 8);  // < 2^31
                 const uint32_t hi = d[2][e] + (d[3][e] << 8);
                 uint32_t v = redc64((uint64_t)hi * 65536u + lo, p, tc.mont);
-                if (FWD && Lp > 1) v = shoup(v, tload<SM>(tw + step * bitrev((uint32_t)m, 4)), p);
+                if (FWD && Lp > 1)
+                    v = shoup(v, SM == TW_STAGE ? tw[m * Lp + G.n1] : tload<SM>(tw + step * bitrev((uint32_t)m, 4)),
+                              p);
                 out.put(G.base + m * st, G.t, G.n0 + m * Lp, v);
             }
         }
@@ -483,7 +501,7 @@ __device__ __forceinline__ void stage_split(int logL, int &nst, int &base, int &
     extra = nst ? logL % nst : 0;
 }
 
-template <bool FWD, bool SM, class TC = NoTc>
+template <bool FWD, int SM, class TC = NoTc>
 __device__ __forceinline__ void run_stage(int b, const TileMap &M, int logL, int logLc,
                                           const uint2 *__restrict__ tw, int logT, uint32_t p,
                                           uint32_t p2, bool hz = false, const TC &tc = TC()) {
@@ -590,7 +608,7 @@ __device__ __forceinline__ void ntt_forward(const TileMap &M, int logL, const ui
 // (radix R, L' = 1) of A and of B, the pointwise product A*B*2^-32
 // (Montgomery), and the first inverse stage, for each group of R
 // consecutive elements; the product is written over A.
-template <int R, bool SM>
+template <int R, int SM>
 __device__ __forceinline__ void stage_fused_pointwise(const TileMap &MA, const TileMap &MB, int logL,
                                                       const uint2 *__restrict__ twf,
                                                       const uint2 *__restrict__ twi, int logT,
@@ -628,20 +646,30 @@ __device__ __forceinline__ void stage_fused_pointwise(const TileMap &MA, const T
 // the remaining inverse stages on A.
 //
 // Twiddles.  COMPACT = false: every stage reads omega_T^{+-e} from twf /
-// twi (T = 2^logT, a multiple of 2^logL), stage i at stride T / Lc_i.
-// COMPACT = true: twf points at one table pair per stage, back to back --
-// stage i's omega_{Lc_i}^e then omega_{Lc_i}^{-e}, e < Lc_i -- so every
-// stage reads at stride 1 and the gathers of a warp stay on distinct
-// shared-memory banks (twi and logT are unused).
+// twi (T = 2^logT, a multiple of 2^logL), stage i at stride T / Lc_i;
+// SM says whether that table is in shared memory.  COMPACT = true: twf
+// points at one block per stage in shared memory, back to back (stage_block
+// gives the layout): stage i's forward entries in the TW_STAGE layout
+// (Lc_i twiddles, then R_i root slots), then its inverse entries (twi and
+// logT are unused).
 //
 // The last inverse stage hands its outputs to out.put; the return value says
 // whether it did (false when the transform has fewer than two stages: the
 // results are then in MA's tile).
-template <bool SM, bool COMPACT, typename WaitB, class Out = TileOut, class TC = NoTc>
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// after_fused() runs once B's tile is no longer read (after the pointwise
+// stage and its barrier), before the inverse stages: a caller may start
+// refilling B's memory there.
+template <bool SM, bool COMPACT, typename WaitB, class Out = TileOut, class TC = NoTc, class Hook = NoHook>
 __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &MB, int logL,
                                              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
                                              int logT, uint32_t p, uint32_t p2, uint32_t mont, WaitB wait_b,
-                                             const Out &out = Out(), const TC &tc = TC()) {
+                                             const Out &out = Out(), const TC &tc = TC(),
+                                             const Hook &after_fused = Hook()) {
+    constexpr int MODE = COMPACT ? TW_STAGE : SM ? TW_SHARED : TW_GLOBAL;
     int nst, base, extra;
     stage_split(logL, nst, base, extra);
     if (nst == 0) {  // length 1: the product of the single values
@@ -653,13 +681,15 @@ __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &M
             *a = montmul(*a, *b, p, mont);
         }
         __syncthreads();
+        after_fused();
         return false;
     }
-    // stage i's tables: (tf, ti, lg)
-    auto tables = [&](const uint2 *tab, int logLc, const uint2 *&tf, const uint2 *&ti, int &lg) {
+    // stage at block offset toff (radix 2^b, sub-block length 2^logLc):
+    // tables (tf, ti, lg); a stage block holds 2 (Lc + R) entries
+    auto tables = [&](int toff, int logLc, int b, const uint2 *&tf, const uint2 *&ti, int &lg) {
         if (COMPACT) {
-            tf = tab;
-            ti = tab + (1 << logLc);
+            tf = twf + toff;
+            ti = tf + (1 << logLc) + (1 << b);
             lg = logLc;
         } else {
             tf = twf;
@@ -672,54 +702,55 @@ __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &M
     for (int pass = 0; pass < 2; ++pass) {
         const TileMap &M = pass ? MB : MA;
         if (pass) wait_b();
-        const uint2 *tab = twf;
-        int logLc = logL;
+        int logLc = logL, toff = 0;
         for (int i = 0; i + 1 < nst; ++i) {
             const int b = base + (i < extra ? 1 : 0);
-            tables(tab, logLc, tf, ti, lg);
-            run_stage<true, SM>(b, M, logL, logLc, tf, lg, p, p2, false, tc);
-            tab += 2 << logLc;
+            tables(toff, logLc, b, tf, ti, lg);
+            run_stage<true, MODE>(b, M, logL, logLc, tf, lg, p, p2, false, tc);
+            toff += 2 * ((1 << logLc) + (1 << b));
             logLc -= b;
         }
     }
-    // the last stage: its tables follow the earlier stages' tables
-    const uint2 *tab = twf;
+    // the last stage (length 2^blast); its block follows the earlier ones
+    const int blast = base + (nst - 1 < extra ? 1 : 0);
+    int toff = 0;
     {
         int logLc = logL;
         for (int i = 0; i + 1 < nst; ++i) {
-            tab += 2 << logLc;
-            logLc -= base + (i < extra ? 1 : 0);
+            const int b = base + (i < extra ? 1 : 0);
+            toff += 2 * ((1 << logLc) + (1 << b));
+            logLc -= b;
         }
     }
-    const int blast = base + (nst - 1 < extra ? 1 : 0);
-    tables(tab, blast, tf, ti, lg);
+    tables(toff, blast, blast, tf, ti, lg);
     switch (blast) {
-        case 1: stage_fused_pointwise<2, SM>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
-        case 2: stage_fused_pointwise<4, SM>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
-        case 3: stage_fused_pointwise<8, SM>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
-        default: stage_fused_pointwise<16, SM>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
+        case 1: stage_fused_pointwise<2, MODE>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
+        case 2: stage_fused_pointwise<4, MODE>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
+        case 3: stage_fused_pointwise<8, MODE>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
+        default: stage_fused_pointwise<16, MODE>(MA, MB, logL, tf, ti, lg, p, p2, mont); break;
     }
+    after_fused();
     int logLc = blast;
     for (int i = nst - 2; i >= 0; --i) {
         const int b = base + (i < extra ? 1 : 0);
         logLc += b;
-        tab -= 2 << logLc;  // stage i's tables precede stage i+1's
-        tables(tab, logLc, tf, ti, lg);
+        toff -= 2 * ((1 << logLc) + (1 << b));  // stage i's block precedes stage i+1's
+        tables(toff, logLc, b, tf, ti, lg);
         if (i > 0) {
-            run_stage<false, SM>(b, MA, logL, logLc, ti, lg, p, p2, false, tc);
+            run_stage<false, MODE>(b, MA, logL, logLc, ti, lg, p, p2, false, tc);
         } else {  // the last inverse stage
             const TileIn in;
             if constexpr (TC::on) {
                 if (b == 4) {
-                    stage_tc16<false, false, SM>(MA, logL, logLc, ti, lg, p, tc, in, out);
+                    stage_tc16<false, false, MODE>(MA, logL, logLc, ti, lg, p, tc, in, out);
                     continue;
                 }
             }
             switch (b) {
-                case 1: stage_dit<2, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
-                case 2: stage_dit<4, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
-                case 3: stage_dit<8, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
-                default: stage_dit<16, SM>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
+                case 1: stage_dit<2, MODE>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
+                case 2: stage_dit<4, MODE>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
+                case 3: stage_dit<8, MODE>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
+                default: stage_dit<16, MODE>(MA, logL, logLc, ti, lg, p, p2, in, out); break;
             }
         }
     }

@@ -235,6 +235,38 @@ struct MidStore {
     }
 };
 
+// The middle pass's twiddles for prime t in shared memory, one block per
+// register stage of the length-Y1a column transform (ntt_stages.cuh,
+// stage_blocks, TW_STAGE): for a stage of radix R and sub-block length
+// Lc = R L', entry m L' + n1 = omega_Lc^{n1 brev(m)} and, after the Lc
+// entries, the roots omega_R^j (j < R/2), forward then inverse; taken from
+// the omega_Y1^{+-e} tables (omega_Lc = omega_Y1^{Y1 / Lc}) by asynchronous
+// copies the caller commits.
+__device__ __forceinline__ void copy_stage_tables(const KParams &P, int t, uint2 *tab) {
+    const PrimeConst &pc = P.pc[t];
+    int nst, sbase, sextra;
+    stage_split(P.logY1a, nst, sbase, sextra);
+    int logLc = P.logY1a, toff = 0;
+    for (int i = 0; i < nst; ++i) {
+        const int b = sbase + (i < sextra ? 1 : 0);
+        const int logLp = logLc - b, sh = P.logY1 - logLc;
+        const int Lc = 1 << logLc, R = 1 << b;
+        uint2 *F = tab + toff;
+        uint2 *I = F + Lc + R;
+        toff += 2 * (Lc + R);
+        for (int idx = threadIdx.x; idx < Lc + R / 2; idx += blockDim.x) {
+            size_t e;
+            if (idx < Lc)
+                e = (size_t)(idx & ((1 << logLp) - 1)) * bitrev((uint32_t)(idx >> logLp), b);
+            else
+                e = (size_t)(idx - Lc) << logLp;  // root omega_R^j = omega_Lc^(j L')
+            cp_async8(F + idx, pc.t1_f + (e << sh));
+            cp_async8(I + idx, pc.t1_i + (e << sh));
+        }
+        logLc -= b;
+    }
+}
+
 // Pass 2 on one tile: columns [cs S, cs S + S) of the rows (pos, i1), prime t,
 // for i1 = Y1a pb + i1a, i1a < Y1a (without a split Y1a = Y1 and pb = 0).
 // SMTW: the omega_Y1 tables, and for every later stage a compact table of
@@ -248,18 +280,10 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     const int twoK = 2 * P.K;
     const int Y1 = (int)P.Y1a;  // this tile's column length
     const PrimeConst &pc = P.pc[t];
-    // SMTW: compact per-stage table pairs, back to back, then the tiles
+    // SMTW: per-stage twiddle blocks (copy_stage_tables), then the tiles
     uint2 *tab = reinterpret_cast<uint2 *>(smem);
-    int nst, sbase, sextra;
-    stage_split(P.logY1a, nst, sbase, sextra);
-    size_t tab_entries = 0;
-    {
-        int logLc = P.logY1a;
-        for (int i = 0; i < nst; ++i) {
-            tab_entries += (size_t)2 << logLc;
-            logLc -= sbase + (i < sextra ? 1 : 0);
-        }
-    }
+    int offs[8];
+    const size_t tab_entries = (size_t)stage_blocks(P.logY1a, offs);
     // Tile layout.  S < 32 (a warp spans several rows): rows of S words at
     // pitch S, one empty row after every R rows, R the radix of the column
     // transform's last stage (TileMap::pl) -- every stage's warp accesses
@@ -275,20 +299,7 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     const uint32_t *ZB = P.Z + (size_t)(t * 2 + 1) * (size_t)P.Y * twoK;
     const size_t base = ((size_t)pos * P.Y1 + (size_t)P.Y1a * pb) * twoK + (size_t)cs * S;
     const TileMap tmp{A, S, S, 1, 0, pitch, 0, pl};
-    if (SMTW) {  // stage i: omega_Lc^{+-e}, e < Lc = entries at stride Y1 / Lc (no split: Y1a = Y1),
-                 // copied asynchronously with A's slice
-        uint2 *f = tab;
-        int logLc = P.logY1a;
-        for (int i = 0; i < nst; ++i) {
-            const int sh = P.logY1 - logLc;
-            for (int e = threadIdx.x; e < (1 << logLc); e += blockDim.x) {
-                cp_async8(f + e, pc.t1_f + ((size_t)e << sh));
-                cp_async8(f + e + (1 << logLc), pc.t1_i + ((size_t)e << sh));
-            }
-            f += (size_t)2 << logLc;
-            logLc -= sbase + (i < sextra ? 1 : 0);
-        }
-    }
+    if (SMTW) copy_stage_tables(P, t, tab);  // copied asynchronously with A's slice
     // A's slice, then B's, as two asynchronous copy groups: B is still in
     // flight while A is transformed.  Rows of S words: 16-byte copies when
     // both ends of every row are 16-byte aligned -- the dense padded layout
@@ -335,6 +346,124 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
         const int i1 = e >> logS, c = e & (S - 1);
         ZA[base + (size_t)i1 * twoK + c] = red(A[(size_t)padded(tmp, i1) * pitch + c], p);
+    }
+}
+
+// Pass 2, persistent form for one product: block b runs the tiles b,
+// b + gridDim.x, ... of the tile list ordered prime-slowest (tile T: prime
+// T / (ncs Y2 Y1b), then pos, pb and the column slice), so a block loads
+// each prime's twiddle tables once rather than once per tile.  Two tile
+// buffers alternate roles: when the pointwise stage of tile i has consumed
+// its second operand, the first operand of tile i+1 starts copying into
+// that buffer while tile i's inverse stages run; when tile i's results are
+// stored, tile i+1's second operand starts copying into the other buffer
+// while tile i+1's first operand is transformed.  Same shared memory as
+// mid_tile, same arithmetic and results.
+template <bool SMTW>
+__device__ __forceinline__ void mid_tiles(const KParams &P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int S = P.S, logS = P.logS;
+    const int twoK = 2 * P.K;
+    const int Y1 = (int)P.Y1a;
+    uint2 *tab = reinterpret_cast<uint2 *>(smem);
+    int offs[8];
+    const size_t tab_entries = (size_t)stage_blocks(P.logY1a, offs);
+    const int pl = mid_pad_log(P.logY1a, S);
+    const int pitch = pl ? S : S + 1;
+    const int rows = pl ? Y1 + (Y1 >> pl) : Y1;
+    uint32_t *X = reinterpret_cast<uint32_t *>(SMTW ? (void *)(tab + tab_entries) : (void *)smem);
+    uint32_t *Ybuf = X + (size_t)rows * pitch + 16;
+    const TileMap tmp{X, S, S, 1, 0, pitch, 0, pl};
+    const bool copy16 = pl && S % 4 == 0;
+    const int ncs = twoK >> logS;
+    const int per_t = ncs * (int)P.Y2 * (int)P.Y1b;
+    const int ntiles = per_t * P.r;
+
+    struct Tile {
+        int t;
+        size_t base;
+    };
+    auto tile_of = [&](int T) {
+        Tile u;
+        u.t = T / per_t;
+        int rem = T - u.t * per_t;
+        const int cs = rem % ncs;
+        rem /= ncs;
+        const int pb = rem & ((int)P.Y1b - 1), pos = rem >> P.logY1b;
+        u.base = ((size_t)pos * P.Y1 + (size_t)P.Y1a * pb) * twoK + (size_t)cs * S;
+        return u;
+    };
+    auto slab = [&](int t, int op) { return P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK; };
+    auto fill = [&](uint32_t *T, const uint32_t *Z, size_t base) {
+        if (copy16) {
+            const int logS4 = logS - 2;
+            for (int e = threadIdx.x; e < Y1 * (S >> 2); e += blockDim.x) {
+                const int i1 = e >> logS4, c4 = (e & ((S >> 2) - 1)) << 2;
+                cp_async16(T + (size_t)padded(tmp, i1) * pitch + c4, Z + base + (size_t)i1 * twoK + c4);
+            }
+        } else {
+            for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+                const int i1 = e >> logS, c = e & (S - 1);
+                cp_async4(T + (size_t)padded(tmp, i1) * pitch + c, Z + base + (size_t)i1 * twoK + c);
+            }
+        }
+    };
+    auto load_tables = [&](int t) { copy_stage_tables(P, t, tab); };
+
+    int T = blockIdx.x;
+    if (T >= ntiles) return;
+    Tile cur = tile_of(T);
+    uint32_t *Pb = X, *Qb = Ybuf;
+    // prologue: tables and the first operand, then the second operand
+    if (SMTW) load_tables(cur.t);
+    fill(Pb, slab(cur.t, 0), cur.base);
+    cp_async_commit();
+    fill(Qb, slab(cur.t, 1), cur.base);
+    cp_async_commit();
+    for (;;) {
+        const int Tn = T + (int)gridDim.x;
+        const bool has_next = Tn < ntiles;
+        const Tile nxt = tile_of(has_next ? Tn : T);
+        const PrimeConst &pc = P.pc[cur.t];
+        const uint32_t p = pc.p, p2 = pc.p2;
+        cp_async_wait<1>();  // this tile's first operand (and tables); its second may still fly
+        __syncthreads();
+        const TileMap am{Pb, S, S, 1, 0, pitch, 0, pl};
+        const TileMap bm{Qb, S, S, 1, 0, pitch, 0, pl};
+        uint32_t *ZA = slab(cur.t, 0);
+        const MidStore out{ZA + cur.base, twoK, p};
+        uint32_t *q_next = Qb;
+        const bool stored = ntt_convolve<SMTW, SMTW>(
+            am, bm, P.logY1a, SMTW ? tab : pc_tables_f(P, cur.t), pc_tables_i(P, cur.t), P.logY1, p, p2, pc.mont,
+            [] {
+                cp_async_wait<0>();
+                __syncthreads();
+            },
+            out, NoTc(), [&] {
+                if (has_next) {  // the second operand is consumed: next tile's first operand into it
+                    fill(q_next, slab(nxt.t, 0), nxt.base);
+                    cp_async_commit();
+                }
+            });
+        if (!stored) {
+            for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+                const int i1 = e >> logS, c = e & (S - 1);
+                ZA[cur.base + (size_t)i1 * twoK + c] = red(Pb[(size_t)padded(tmp, i1) * pitch + c], p);
+            }
+            __syncthreads();
+        }
+        if (!has_next) break;
+        if (SMTW && nxt.t != cur.t) {  // the old tables are no longer read
+            load_tables(nxt.t);
+            cp_async_commit();
+        }
+        fill(Pb, slab(nxt.t, 1), nxt.base);  // next tile's second operand into the freed buffer
+        cp_async_commit();
+        uint32_t *tmpb = Pb;
+        Pb = Qb;
+        Qb = tmpb;
+        T = Tn;
+        cur = nxt;
     }
 }
 
