@@ -817,6 +817,45 @@ def measure_product(ipm, torch, key, plain_path, steps, warmup, flush, stream, k
     return res
 
 
+def measure_ks_comparator(ipm, torch, steps, flush, stream):
+    """The GPU Kronecker-substitution product (ks=1: the integer product
+    a(2^s) b(2^s) by the transform path, the paper's KS_s comparator) next
+    to the chosen form, on the shapes where KS fits the transform length
+    (the small dense workload and the paper's table shapes d = N = 2^9 ..
+    2^11); outputs must agree byte for byte."""
+    rows = []
+    shapes = [("small_dense: d=1024, 255-bit, seed 0", W.small_dense(seed=0))]
+    for k in (9, 10, 11):
+        rng = np.random.default_rng(k)
+        d = 1 << k
+        shapes.append(("paper_table: d = N = 2^%d, seed %d" % (k, k),
+                       (W.Product(d, d, d, d), W.random_poly(rng, d, d), W.random_poly(rng, d, d))))
+    for name, (sh, a, b) in shapes:
+        shape = (sh.na, sh.nb, sh.bits_a, sh.bits_b)
+        da, dan = ipm.to_device(*a)
+        db, dbn = ipm.to_device(*b)
+        res = {"workload": name}
+        outs = {}
+        for label, kw in (("ks", {"ks": 1}), ("chosen", {})):
+            flags = 0 if kw else chosen_flags(ipm, shape, False)[0]
+            plan = ipm.Plan(shape, flags=flags, **kw)
+            c, cn = plan.empty_output()
+            for _ in range(3):
+                plan.mul(da, dan, db, dbn, c, cn)
+            plan.sync()
+            res[label + "_ms"] = timed_ms(torch, lambda: plan.mul(da, dan, db, dbn, c, cn, stream=stream),
+                                          steps, flush, stream)
+            plan.sync()
+            outs[label] = (c, cn)
+            plan.close()
+        if not (torch.equal(outs["ks"][0], outs["chosen"][0]) and torch.equal(outs["ks"][1], outs["chosen"][1])):
+            raise SystemExit("Kronecker substitution and the chosen form disagree on " + name)
+        res["chosen_over_ks"] = res["ks_ms"] / res["chosen_ms"]
+        rows.append(res)
+    return {"path": "ks=1: digit polynomials of a(2^s), b(2^s) multiplied by the transform path, slots unpacked",
+            "rows": rows}
+
+
 def product_summary(r, sm_max):
     """The extra-workload entry of the JSON line."""
     info = r["info"]
@@ -973,6 +1012,8 @@ def run_ours(args):
             extras[key] = product_summary(r, sm_max)
             torch.cuda.empty_cache()
         extras["batch"] = measure_batch(ipm, torch, max(3, args.steps // 4), 3, args.plain, flush)
+        torch.cuda.empty_cache()
+        extras["ks_comparator"] = measure_ks_comparator(ipm, torch, max(3, args.steps // 4), flush, stream)
         torch.cuda.empty_cache()
 
     cpu = None

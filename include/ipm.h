@@ -115,9 +115,19 @@ typedef struct {
  *        c_k = sum a_i b_{k-i} by direct 32-bit limb products, one block per
  *        output coefficient (small products only: La + Lb <= 256 and
  *        na nb La Lb <= 2^27); the other fields must then be 0.
+ *   ks: 1 = Kronecker substitution (§1, §4: the comparison method KS_s):
+ *        c is read off the integer product a(2^s) b(2^s), s = 32 (Lc + 3),
+ *        whose digit polynomials (na (Lc+3) and nb (Lc+3) coefficients of
+ *        32 bits) are multiplied by the transform path (K, M, r, y2, s and
+ *        y1b then apply to that product; kron and school must be 0).  Needs
+ *        (na + nb) (Lc + 3) - 1 <= 2^21 (IPM_ERR_UNSUPPORTED otherwise).
+ *   kara: L >= 1 = the Karatsuba family: L levels of Karatsuba's
+ *        three-product recursion over y (§1 lists Karatsuba among the plain
+ *        methods), the schoolbook kernel at the leaves; the other fields
+ *        must then be 0 (small products: see ipm_karatsuba limits).
  */
 typedef struct {
-    int32_t K, M, r, y2, s, y1b, kron, school;
+    int32_t K, M, r, y2, s, y1b, kron, school, ks, kara;
 } ipm_params;
 
 /* What a plan chose (ipm_choose / ipm_get_info). */
@@ -138,6 +148,10 @@ typedef struct {
     int64_t kron_na, kron_nb; /* packed coefficient counts */
     uint32_t kron_bits_a, kron_bits_b;  /* packed bit bounds */
     int32_t school;           /* 1: schoolbook family (K, M, r, Y... are 0) */
+    int32_t ks;               /* 1: Kronecker substitution; K, M, r, Y...
+                                 describe the product of the digit polynomials */
+    int32_t ks_w;             /* limbs per slot (Lc + 3), 0 when ks = 0 */
+    int32_t kara;             /* Karatsuba levels (0: not that family) */
 } ipm_plan_info;
 
 /*

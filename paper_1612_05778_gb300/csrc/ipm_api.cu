@@ -70,8 +70,8 @@ ipm_status run_product(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a,
     if (!aligned16(a) || !aligned16(b) || !aligned16(c)) return IPM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const bool prof = plan->profiling;
-    // (packed and schoolbook plans are timed as one phase)
-    if (!prof || sp.kr.s > 1 || sp.school)
+    // (packed, substituted and schoolbook plans are timed as one phase)
+    if (!prof || sp.kr.s > 1 || sp.school || sp.ks.on)
         return launch_product(sp, a, an, b, bn, c, cn, stream) ? IPM_ERR_CUDA : IPM_OK;
     // profiled: events around the three passes (a split plan's outer
     // passes count with the middle one)

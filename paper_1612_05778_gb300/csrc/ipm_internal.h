@@ -137,8 +137,25 @@ struct KronPlan {
     size_t off_a, off_an, off_b, off_bn, off_c, off_cn;  // word offsets from Z
 };
 
+// Kronecker substitution (ipm_ks.cu): the product read off the integer
+// product a(2^s) b(2^s), s = 32 w, w = lc + 3 limbs per slot; the integer
+// product is the transform product (kp) of the operands' digit
+// polynomials (na w and nb w coefficients of 32 bits).  Buffers after the
+// transform workspace (word offsets from Z): the digit polynomials, their
+// product (lc' limbs per digit), and per slot t <= nc the low s bits L_t,
+// the high part H_t (int64) and the top bit of L_t.
+struct KsPlan {
+    int32_t on;
+    int32_t w;
+    int64_t na, nb, nc;
+    int32_t la, lb, lc;
+    uint32_t bits_a, bits_b;
+    size_t off_a, off_an, off_b, off_bn, off_c, off_cn, off_L, off_H, off_g;
+};
+
 struct ShapePlan {
     ipm_plan_info info;
+    KsPlan ks;            // on = 0: not the Kronecker-substitution family
     KronPlan kr;          // s = 1: no packing (kp describes the product itself)
     bool school;          // schoolbook family: only kp's shape fields and err are used
     KParams kp;           // pointers filled in by ipm_plan
@@ -189,8 +206,11 @@ int launch_transform_product(const ShapePlan &sp, const uint32_t *a, const uint8
 // Pack, transform product of the packed operands, unpack (ipm_kron.cu).
 int launch_kron_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                         const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
-// One whole product: launch_kron_product when sp.kr.s > 1, else
-// launch_transform_product.
+// Pack, integer product of the digit polynomials, unpack (ipm_ks.cu).
+int launch_ks_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                      const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
+// One whole product: launch_kron_product when sp.kr.s > 1, launch_ks_product
+// for the Kronecker-substitution family, else launch_transform_product.
 int launch_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                    const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
 // The schoolbook family (ipm_school.cu): limits, shared memory, launch.
@@ -200,7 +220,7 @@ size_t school_smem(const KParams &kp);
 int launch_school(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b, const uint8_t *bn,
                   uint32_t *c, uint8_t *cn, void *stream);
 // Products a batched call runs one at a time (split, packed or schoolbook).
-inline bool runs_alone(const ShapePlan &sp) { return sp.school || sp.kp.Y1b > 1 || sp.kr.s > 1; }
+inline bool runs_alone(const ShapePlan &sp) { return sp.school || sp.kp.Y1b > 1 || sp.kr.s > 1 || sp.ks.on; }
 int set_kernel_attributes();
 // Evaluation point for a seed, and the check c(t) = a(t) b(t) mod 2^61 - 1
 // of one product laid out as I describes (ERRBIT_MISMATCH into *err).

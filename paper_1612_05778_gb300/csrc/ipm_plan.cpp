@@ -401,7 +401,65 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
     kr.lc = (int)((sh.bits_a + sh.bits_b + (uint32_t)ilog2((uint64_t)std::min(na, nb)) + 31) / 32);
     kr.bits_a = sh.bits_a;
     kr.bits_b = sh.bits_b;
-    if (P.school < 0 || P.school > 1) return IPM_ERR_ARG;
+    if (P.school < 0 || P.school > 1 || P.ks < 0 || P.ks > 1 || P.kara < 0) return IPM_ERR_ARG;
+    if (P.ks) {  // Kronecker substitution: the digit polynomials' product
+        if (P.kron > 1 || P.school || P.kara) return IPM_ERR_ARG;
+        const int w = kr.lc + 3;
+        const int64_t nA = na * w, nB = nb * w;
+        if (nA + nB - 1 > (1ll << PRIME_ORDER_LOG2)) return IPM_ERR_UNSUPPORTED;
+        const ipm_shape inner{nA - 1, nB - 1, 32, 32};
+        ipm_params Q = P;
+        Q.ks = 0;
+        Q.kron = 0;
+        const ipm_status st = choose_plan_direct(inner, &Q, sp);
+        if (st != IPM_OK) return st;
+        sp.school = false;
+        sp.kr = kr;
+        KsPlan &k = sp.ks;
+        k.on = 1;
+        k.w = w;
+        k.na = na;
+        k.nb = nb;
+        k.nc = kr.nc;
+        k.la = kr.la;
+        k.lb = kr.lb;
+        k.lc = kr.lc;
+        k.bits_a = sh.bits_a;
+        k.bits_b = sh.bits_b;
+        const KParams &kp = sp.kp;
+        const int64_t nslots = kr.nc + 1;
+        size_t at = round4(sp.z_words);
+        k.off_a = at;  at = round4(at + (size_t)nA);
+        k.off_an = at; at = round4(at + ((size_t)nA + 3) / 4);
+        k.off_b = at;  at = round4(at + (size_t)nB);
+        k.off_bn = at; at = round4(at + ((size_t)nB + 3) / 4);
+        k.off_c = at;  at = round4(at + (size_t)kp.nc * kp.lc);
+        k.off_cn = at; at = round4(at + ((size_t)kp.nc + 3) / 4);
+        k.off_L = at;  at = round4(at + (size_t)nslots * w);
+        k.off_H = at;  at = round4(at + 2 * (size_t)nslots);
+        k.off_g = at;  at = round4(at + ((size_t)nslots + 3) / 4);
+        ipm_plan_info &I = sp.info;
+        I.workspace_bytes += (at - sp.z_words) * 4;
+        sp.z_words = at;
+        I.na = na;
+        I.nb = nb;
+        I.nc = kr.nc;
+        I.la = kr.la;
+        I.lb = kr.lb;
+        I.lc = kr.lc;
+        I.kron = 1;
+        I.kron_w = 0;
+        I.kron_na = na;
+        I.kron_nb = nb;
+        I.kron_bits_a = sh.bits_a;
+        I.kron_bits_b = sh.bits_b;
+        I.school = 0;
+        I.ks = 1;
+        I.ks_w = w;
+        I.kara = 0;
+        return IPM_OK;
+    }
+    if (P.kara) return IPM_ERR_UNSUPPORTED;  // the Karatsuba family (ipm_kara.cu) plans below
     if (P.school) {
         if (P.K || P.M || P.r || P.y2 || P.s || P.y1b || P.kron > 1) return IPM_ERR_ARG;
         if (kr.la + kr.lb > SCHOOL_MAX_COLUMNS) return IPM_ERR_ARG;

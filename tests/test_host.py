@@ -190,3 +190,29 @@ def test_plan_free_calls_reject_a_narrow_output_on_the_host():
             ipm.mul_noalloc(na, nb, ba, bb, a, an, b, bn, c, cn)
         with pytest.raises(ValueError, match="c must have shape"):
             ipm.validate(na, nb, ba, bb, a, an, b, bn, c, cn)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1, 1), (1024, 1024, 255, 255), (300, 2, 64, 4096), (2048, 2048, 2048, 2048)])
+def test_kronecker_substitution_plans(shape):
+    """ks=1: slots of w = Lc + 3 limbs; the digit product multiplies
+    polynomials of na w and nb w 32-bit coefficients, within the 2^21
+    transform length."""
+    na, nb, ba, bb = shape
+    I = ipm.choose(*shape, ks=1)
+    base = ipm.choose(*shape)
+    assert I["ks"] == 1 and I["ks_w"] == base["lc"] + 3
+    assert (I["na"], I["nb"], I["nc"], I["lc"]) == (na, nb, na + nb - 1, base["lc"])
+    w = I["ks_w"]
+    assert I["Y"] >= (na + nb) * w - 1 and I["Y"] <= 1 << 21
+    assert I["workspace_bytes"] > base["workspace_bytes"] // 4
+
+
+def test_kronecker_substitution_limits():
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(4096, 4096, 4096, 4096, ks=1)  # (na + nb) w > 2^21
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(100, 100, 64, 64, ks=1, kron=2)
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(100, 100, 64, 64, ks=1, school=1)
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(100, 100, 64, 64, ks=2)
