@@ -1,7 +1,7 @@
 """Benchmark: exact dense Z[y] products on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload huge_dense|large_dense|small_dense|large_all_ones|huge_mixed|batch|taylor|paper_table]
+                    [--workload huge_dense|large_dense|small_dense|large_all_ones|huge_mixed|batch|taylor|paper_table|families]
 
 One step is one whole product c = a*b (split, forward 2-D transforms over
 every prime, pointwise products, inverse transforms, CRT, recombination)
@@ -34,6 +34,10 @@ as 4096 ipm_mul calls (the plain path);
 
 --workload paper_table times the shapes of the paper's own table (d = N =
 2^9 .. 2^16) and lists the paper's 48-core CVL_p^2 seconds beside each row.
+
+--workload families times every product family (learned dispatch, 2-D
+transform, schoolbook, Karatsuba with 1..4 levels, Kronecker substitution)
+on a grid of balanced shapes.
 
 --workload taylor times ipm_taylor_shift, g(x) = f(x + 1), on 2^14
 coefficients below 2^4096 (seed 5), and prints its own line (shifts/s).
@@ -630,6 +634,71 @@ def run_taylor(args):
     return 0
 
 
+FAMILY_GRID = [(d, bits) for d in (64, 256, 1024, 4096) for bits in (32, 256, 2048)]
+
+
+def run_families(args):
+    """Every product family on a grid of balanced shapes (d coefficients
+    of `bits` bits, seed d + bits): the chosen form (learned dispatch), the
+    analytic planner's 2-D transform, the schoolbook family, Karatsuba over
+    y with 1..4 levels and Kronecker substitution, each timed on the same
+    inputs (CUDA events, L2 flushed) where its limits admit the shape; all
+    outputs must agree byte for byte.  The value is the chosen form's
+    products/s on the largest shape."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1612_05778_gb300 import build as ipm_build
+    ipm_build.build()
+    import paper_1612_05778_gb300 as ipm
+    from paper_1612_05778_gb300 import costmodel as cmod
+    cmod.install(points=cmod.load_sweep()["points"])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    fams = [("chosen", {}, ipm.IPM_COSTMODEL), ("transform", {}, 0), ("school", {"school": 1}, 0)] + \
+        [("kara%d" % L, {"kara": L}, 0) for L in (1, 2, 3, 4)] + [("ks", {"ks": 1}, 0)]
+    rows = []
+    for d, bits in FAMILY_GRID:
+        rng = np.random.default_rng(d + bits)
+        a, b = W.random_poly(rng, d, bits), W.random_poly(rng, d, bits)
+        da, dan = ipm.to_device(*a)
+        db, dbn = ipm.to_device(*b)
+        row = {"d": d, "bits": bits, "ms": {}}
+        ref = None
+        for label, kw, flags in fams:
+            try:
+                plan = ipm.Plan((d, d, bits, bits), flags=flags, **kw)
+            except ipm.IpmError:
+                continue  # outside the family's limits
+            c, cn = plan.empty_output()
+            for _ in range(args.warmup):
+                plan.mul(da, dan, db, dbn, c, cn)
+            plan.sync()
+            row["ms"][label] = timed_ms(torch, lambda: plan.mul(da, dan, db, dbn, c, cn, stream=stream),
+                                        args.steps, flush, stream)
+            plan.sync()
+            if ref is None:
+                ref = (c.clone(), cn.clone())
+            elif not (torch.equal(ref[0], c) and torch.equal(ref[1], cn)):
+                raise SystemExit("family %s disagrees at d=%d bits=%d" % (label, d, bits))
+            plan.close()
+        others = {k: v for k, v in row["ms"].items() if k != "chosen"}
+        row["fastest"] = min(others, key=others.get)
+        if "school" in row["ms"]:
+            karas = [v for k, v in row["ms"].items() if k.startswith("kara")]
+            if karas:
+                row["best_karatsuba_over_school"] = row["ms"]["school"] / min(karas)
+        rows.append(row)
+    top = rows[-1]
+    line = {"metric": METRIC, "value": 1e3 / top["ms"]["chosen"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": top["ms"]["chosen"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "families: d in {64, 256, 1024, 4096} x bits in {32, 256, 2048}, balanced, "
+                                   "signed uniform, seed d + bits; value = d=4096, 2048-bit"},
+            "rows": rows}
+    print(json.dumps(line))
+    return 0
+
+
 # The paper's own benchmark (§4, Table classical4andCVL2): random dense
 # polynomials with degree d equal to the coefficient size N, CVL_p^2 on a
 # 48-core AMD Opteron 6168 (900 MHz), seconds per product.  Context only:
@@ -1078,7 +1147,7 @@ def main(argv=None):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("taylor", "paper_table"):
+    if args.workload in ("taylor", "paper_table", "families"):
         # one-GPU measurements: under torchrun only rank 0 runs them
         world, rank, _ = dist_env()
         if world > 1 and rank != 0:
@@ -1089,6 +1158,8 @@ def main(argv=None):
         return run_taylor(args)
     if args.workload == "paper_table":
         return run_paper_table(args)
+    if args.workload == "families":
+        return run_families(args)
     return run_ours(args)
 
 

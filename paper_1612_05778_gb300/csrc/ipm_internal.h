@@ -153,8 +153,27 @@ struct KsPlan {
     size_t off_a, off_an, off_b, off_bn, off_c, off_cn, off_L, off_H, off_g;
 };
 
+// The Karatsuba family (ipm_kara.cu): `levels` levels over y, operands
+// padded to n2 = m 2^levels, 3^levels schoolbook leaves of m x m
+// coefficients (kp describes one leaf product: m, m, lla / llb limbs,
+// bits + levels, output stride lci).  Buffers after nothing else (word
+// offsets from Z): leaf operands and signs, then the products of every
+// level d = 1 .. levels (3^d products of 2 n2 / 2^d - 1 coefficients, lci
+// limbs each) and their signs; level 0 is the output c.
+constexpr int KARA_MAX_LEVELS = 4;
+struct KaraPlan {
+    int32_t levels;  // 0: not this family
+    int64_t n2, m;
+    int64_t na, nb, nc;
+    int32_t la, lb, lc, lla, llb, lci;
+    uint32_t bits_a, bits_b;
+    size_t off_a, off_an, off_b, off_bn;
+    size_t off_lev[KARA_MAX_LEVELS + 1], off_levn[KARA_MAX_LEVELS + 1];
+};
+
 struct ShapePlan {
     ipm_plan_info info;
+    KaraPlan ka;          // levels = 0: not the Karatsuba family
     KsPlan ks;            // on = 0: not the Kronecker-substitution family
     KronPlan kr;          // s = 1: no packing (kp describes the product itself)
     bool school;          // schoolbook family: only kp's shape fields and err are used
@@ -206,6 +225,13 @@ int launch_transform_product(const ShapePlan &sp, const uint32_t *a, const uint8
 // Pack, transform product of the packed operands, unpack (ipm_kron.cu).
 int launch_kron_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                         const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
+// Leaf operands, batched schoolbook leaves, level-by-level combination
+// (ipm_kara.cu); `count` equal-shape schoolbook products back to back
+// (ipm_school.cu).
+int launch_kara_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                        const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
+int launch_school_batch(const KParams &kp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                        const uint8_t *bn, uint32_t *c, uint8_t *cn, int64_t count, void *stream);
 // Pack, integer product of the digit polynomials, unpack (ipm_ks.cu).
 int launch_ks_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                       const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
@@ -220,7 +246,9 @@ size_t school_smem(const KParams &kp);
 int launch_school(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b, const uint8_t *bn,
                   uint32_t *c, uint8_t *cn, void *stream);
 // Products a batched call runs one at a time (split, packed or schoolbook).
-inline bool runs_alone(const ShapePlan &sp) { return sp.school || sp.kp.Y1b > 1 || sp.kr.s > 1 || sp.ks.on; }
+inline bool runs_alone(const ShapePlan &sp) {
+    return sp.school || sp.kp.Y1b > 1 || sp.kr.s > 1 || sp.ks.on || sp.ka.levels;
+}
 int set_kernel_attributes();
 // Evaluation point for a seed, and the check c(t) = a(t) b(t) mod 2^61 - 1
 // of one product laid out as I describes (ERRBIT_MISMATCH into *err).

@@ -29,52 +29,12 @@
 
 #include <algorithm>
 
+#include "carry.cuh"
 #include "ipm_internal.h"
 
 namespace ipm {
 
 namespace {
-
-// Warp-wide carrying of a signed multi-limb sum, 32 limbs per call, low
-// chunks first.  Lane value P (|P| < 2^40) is the contribution to limb
-// q = q0 + lane of X = sum_q P_q 2^(32 q).  Writing P_q = t_q + 2^32 h_q,
-// adding h_(q-1) to t_q leaves t'_q + 2^32 g_q with g_q in {-1, 0, 1};
-// the +1 and -1 carries one limb up are then resolved as an addition and
-// a subtraction by ballot carry-lookahead (33-bit integer addition of the
-// generate and propagate masks).  Returns limb q of X modulo 2^(32 n), two's
-// complement; `state` carries (h, g, carry, borrow) between chunks.
-struct CarryState {
-    int h = 0, g = 0;
-    unsigned cplus = 0, cminus = 0;
-};
-
-__device__ __forceinline__ unsigned ks_lookahead(unsigned gen, unsigned prop, unsigned *cio) {
-    const uint64_t s = (uint64_t)gen + (uint64_t)(gen | prop) + *cio;
-    *cio = (unsigned)(s >> 32);
-    return (unsigned)s ^ prop;
-}
-
-__device__ __forceinline__ uint32_t carry_chunk(int64_t P, bool act, CarryState &st) {
-    const int lane = threadIdx.x & 31;
-    const int h = act ? (int)(P >> 32) : 0;
-    int hprev = __shfl_up_sync(0xffffffffu, h, 1);
-    if (lane == 0) hprev = st.h;
-    const int64_t sum = (act ? (int64_t)(uint32_t)P : 0) + hprev;
-    const uint32_t tq = (uint32_t)sum;
-    const int g = (int)(sum >> 32);
-    int gprev = __shfl_up_sync(0xffffffffu, g, 1);
-    if (lane == 0) gprev = st.g;
-    st.h = __shfl_sync(0xffffffffu, h, 31);
-    st.g = __shfl_sync(0xffffffffu, g, 31);
-    const uint32_t gp = gprev == 1 ? 1u : 0u;
-    const unsigned cm = ks_lookahead(__ballot_sync(0xffffffffu, gp && tq == 0xffffffffu),
-                                     __ballot_sync(0xffffffffu, tq + gp == 0xffffffffu), &st.cplus);
-    const uint32_t u = tq + gp + ((cm >> lane) & 1u);
-    const uint32_t gm = gprev == -1 ? 1u : 0u;
-    const unsigned bm = ks_lookahead(__ballot_sync(0xffffffffu, gm && u == 0u),
-                                     __ballot_sync(0xffffffffu, u == gm), &st.cminus);
-    return u - gm - ((bm >> lane) & 1u);
-}
 
 // Signed value of limb l of product digit k (le limbs each, sign byte).
 __device__ __forceinline__ int64_t signed_limb(const uint32_t *e, const uint8_t *en, int le, int64_t k, int l) {

@@ -459,7 +459,71 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
         I.kara = 0;
         return IPM_OK;
     }
-    if (P.kara) return IPM_ERR_UNSUPPORTED;  // the Karatsuba family (ipm_kara.cu) plans below
+    if (P.kara) {  // the Karatsuba family over y with schoolbook leaves
+        if (P.kara > KARA_MAX_LEVELS || P.K || P.M || P.r || P.y2 || P.s || P.y1b || P.kron > 1 || P.school)
+            return IPM_ERR_ARG;
+        const int L = P.kara;
+        const int64_t n = std::max(na, nb);
+        const int64_t m = (n + (1ll << L) - 1) >> L, n2 = m << L;
+        KaraPlan k{};
+        k.levels = L;
+        k.n2 = n2;
+        k.m = m;
+        k.na = na;
+        k.nb = nb;
+        k.nc = kr.nc;
+        k.la = kr.la;
+        k.lb = kr.lb;
+        k.lc = kr.lc;
+        k.bits_a = sh.bits_a;
+        k.bits_b = sh.bits_b;
+        k.lla = (int)((sh.bits_a + L + 31) / 32);
+        k.llb = (int)((sh.bits_b + L + 31) / 32);
+        // every node product at depth d is below len 2^(bits_a + d) 2^(bits_b + d) <= n2 2^(bits_a + bits_b + 2L)
+        k.lci = (int)((sh.bits_a + sh.bits_b + 2 * L + ilog2((uint64_t)n2) + 1 + 31) / 32);
+        if (k.lla + k.llb > SCHOOL_MAX_COLUMNS) return IPM_ERR_ARG;
+        if ((double)m * (double)m * k.lla * k.llb > SCHOOL_MAX_LIMB_PRODUCTS) return IPM_ERR_ARG;
+        int64_t leaves = 1;
+        for (int d = 0; d < L; ++d) leaves *= 3;
+        size_t at = 0;
+        k.off_a = at;  at = round4(at + (size_t)(leaves * m) * k.lla);
+        k.off_an = at; at = round4(at + ((size_t)(leaves * m) + 3) / 4);
+        k.off_b = at;  at = round4(at + (size_t)(leaves * m) * k.llb);
+        k.off_bn = at; at = round4(at + ((size_t)(leaves * m) + 3) / 4);
+        int64_t nodes = 1;
+        for (int d = 0; d <= L; ++d) {
+            const int64_t len = n2 >> d, cnt = nodes * (2 * len - 1);
+            if (d > 0) {
+                k.off_lev[d] = at;  at = round4(at + (size_t)cnt * k.lci);
+                k.off_levn[d] = at; at = round4(at + ((size_t)cnt + 3) / 4);
+            }
+            nodes *= 3;
+        }
+        ShapePlan s{};
+        s.school = false;
+        s.kr = kr;
+        s.ka = k;
+        s.z_words = at;
+        ipm_plan_info &I = s.info;
+        I.na = na; I.nb = nb; I.nc = kr.nc;
+        I.la = kr.la; I.lb = kr.lb; I.lc = kr.lc;
+        I.Y1b = 1;
+        I.kron = 1;
+        I.kron_na = na;
+        I.kron_nb = nb;
+        I.kron_bits_a = sh.bits_a;
+        I.kron_bits_b = sh.bits_b;
+        I.kara = L;
+        I.workspace_bytes = at * 4;
+        KParams &kp = s.kp;  // one leaf product (schoolbook)
+        std::memset(&kp, 0, sizeof(kp));
+        kp.na = m; kp.nb = m; kp.nc = 2 * m - 1;
+        kp.la = k.lla; kp.lb = k.llb; kp.lc = k.lci;
+        kp.bits_a = sh.bits_a + (uint32_t)L; kp.bits_b = sh.bits_b + (uint32_t)L;
+        kp.Y1b = 1;
+        sp = s;
+        return IPM_OK;
+    }
     if (P.school) {
         if (P.K || P.M || P.r || P.y2 || P.s || P.y1b || P.kron > 1) return IPM_ERR_ARG;
         if (kr.la + kr.lb > SCHOOL_MAX_COLUMNS) return IPM_ERR_ARG;

@@ -29,6 +29,17 @@ __global__ void __launch_bounds__(SCHOOL_THREADS) k_school(const __grid_constant
     extern __shared__ __align__(16) unsigned char smem[];
     long long *col = reinterpret_cast<long long *>(smem);  // La + Lb + 1 signed column sums, then limbs
     const int64_t k = blockIdx.x;
+    // several products of one shape (Karatsuba leaves): product blockIdx.y,
+    // operands and result back to back
+    {
+        const int64_t y = blockIdx.y;
+        a += y * P.na * P.la;
+        an += y * P.na;
+        b += y * P.nb * P.lb;
+        bn += y * P.nb;
+        c += y * P.nc * P.lc;
+        cn += y * P.nc;
+    }
     const int la = P.la, lb = P.lb, lc = P.lc;
     const int ncol = la + lb;
     if (threadIdx.x == 0) {
@@ -90,6 +101,14 @@ __global__ void __launch_bounds__(SCHOOL_THREADS) k_school(const __grid_constant
 }  // namespace
 
 size_t school_smem(const KParams &kp) { return ((size_t)kp.la + kp.lb + 1) * (sizeof(long long) + sizeof(uint32_t)); }
+
+int launch_school_batch(const KParams &kp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                        const uint8_t *bn, uint32_t *c, uint8_t *cn, int64_t count, void *stream) {
+    dim3 grid((unsigned)kp.nc, (unsigned)count, 1);
+    k_school<<<grid, SCHOOL_THREADS, school_smem(kp), (cudaStream_t)stream>>>(kp, a, an, b, bn, c, cn);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int launch_school(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b, const uint8_t *bn,
                   uint32_t *c, uint8_t *cn, void *stream) {

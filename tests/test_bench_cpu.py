@@ -49,7 +49,7 @@ def test_stage_bits(logL, want):
     assert sum(want) == logL
 
 
-@pytest.mark.parametrize("workload", ["taylor", "paper_table"])
+@pytest.mark.parametrize("workload", ["taylor", "paper_table", "families"])
 def test_single_gpu_workloads_leave_other_ranks_idle(workload, monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     monkeypatch.setenv("RANK", "1")

@@ -216,3 +216,25 @@ def test_kronecker_substitution_limits():
         ipm.choose(100, 100, 64, 64, ks=1, school=1)
     with pytest.raises(ipm.IpmError):
         ipm.choose(100, 100, 64, 64, ks=2)
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(1, 1, 1, 1), (1000, 1000, 255, 255), (700, 1500, 1000, 64), (3, 2000, 64, 64)])
+def test_karatsuba_plans(shape, levels):
+    """kara=L: operands padded to n2 = m 2^L >= max(na, nb), m < max(na,
+    nb) / 2^L + 1; the output layout is the product's own."""
+    na, nb, ba, bb = shape
+    I = ipm.choose(*shape, kara=levels)
+    base = ipm.choose(*shape)
+    assert I["kara"] == levels and I["K"] == 0 and I["r"] == 0
+    assert (I["na"], I["nb"], I["nc"], I["lc"]) == (na, nb, na + nb - 1, base["lc"])
+    assert I["workspace_bytes"] > 0
+
+
+def test_karatsuba_limits():
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(100, 100, 64, 64, kara=5)
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(100, 100, 64, 64, kara=2, K=8)
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(100, 100, 8192, 8192, kara=1)  # leaf columns beyond the schoolbook kernel's
