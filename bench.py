@@ -36,8 +36,8 @@ as 4096 ipm_mul calls (the plain path);
 2^9 .. 2^16) and lists the paper's 48-core CVL_p^2 seconds beside each row.
 
 --workload families times every product family (learned dispatch, 2-D
-transform, schoolbook, Karatsuba with 1..4 levels, Kronecker substitution)
-on a grid of balanced shapes.
+transform, schoolbook, Karatsuba with 1..4 levels, Kronecker substitution,
+the big-prime form) on a grid of balanced shapes.
 
 --workload taylor times ipm_taylor_shift, g(x) = f(x + 1), on 2^14
 coefficients below 2^4096 (seed 5), and prints its own line (shifts/s).
@@ -641,7 +641,8 @@ def run_families(args):
     """Every product family on a grid of balanced shapes (d coefficients
     of `bits` bits, seed d + bits): the chosen form (learned dispatch), the
     analytic planner's 2-D transform, the schoolbook family, Karatsuba over
-    y with 1..4 levels and Kronecker substitution, each timed on the same
+    y with 1..4 levels, Kronecker substitution and the big-prime form (one
+    generalized Fermat prime), each timed on the same
     inputs (CUDA events, L2 flushed) where its limits admit the shape; all
     outputs must agree byte for byte.  The value is the chosen form's
     products/s on the largest shape."""
@@ -655,7 +656,7 @@ def run_families(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     fams = [("chosen", {}, ipm.IPM_COSTMODEL), ("transform", {}, 0), ("school", {"school": 1}, 0)] + \
-        [("kara%d" % L, {"kara": L}, 0) for L in (1, 2, 3, 4)] + [("ks", {"ks": 1}, 0)]
+        [("kara%d" % L, {"kara": L}, 0) for L in (1, 2, 3, 4)] + [("ks", {"ks": 1}, 0), ("bigp", {"bigp": 1}, 0)]
     rows = []
     for d, bits in FAMILY_GRID:
         rng = np.random.default_rng(d + bits)

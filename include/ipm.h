@@ -123,11 +123,17 @@ typedef struct {
  *        (na + nb) (Lc + 3) - 1 <= 2^21 (IPM_ERR_UNSUPPORTED otherwise).
  *   kara: L >= 1 = the Karatsuba family: L levels of Karatsuba's
  *        three-product recursion over y (§1 lists Karatsuba among the plain
- *        methods), the schoolbook kernel at the leaves; the other fields
- *        must then be 0 (small products: see ipm_karatsuba limits).
+ *        methods), the schoolbook kernel at the leaves (L <= 4; the leaf
+ *        operands, of bits + L bits, must fit the schoolbook limits); the
+ *        other fields must then be 0.
+ *   bigp: 1 = the big-prime form (§3.1, §4): the same two convolutions
+ *        modulo ONE generalized Fermat prime p = (2^63 + 2^53)^2 + 1 instead
+ *        of several 30-bit primes and CRT (K may be set; the planner takes
+ *        the smallest K with 4H < p and Y <= 2^21; the other fields must be
+ *        0).  Simple radix-2 kernels: meant for small products.
  */
 typedef struct {
-    int32_t K, M, r, y2, s, y1b, kron, school, ks, kara;
+    int32_t K, M, r, y2, s, y1b, kron, school, ks, kara, bigp;
 } ipm_params;
 
 /* What a plan chose (ipm_choose / ipm_get_info). */
@@ -152,6 +158,7 @@ typedef struct {
                                  describe the product of the digit polynomials */
     int32_t ks_w;             /* limbs per slot (Lc + 3), 0 when ks = 0 */
     int32_t kara;             /* Karatsuba levels (0: not that family) */
+    int32_t bigp;             /* 1: big-prime form (K, M, N, Y describe it; r = 1) */
 } ipm_plan_info;
 
 /*

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("M", ctypes.c_int32), ("r", ctypes.c_int32),
                 ("y2", ctypes.c_int32), ("s", ctypes.c_int32), ("y1b", ctypes.c_int32),
                 ("kron", ctypes.c_int32), ("school", ctypes.c_int32), ("ks", ctypes.c_int32),
-                ("kara", ctypes.c_int32)]
+                ("kara", ctypes.c_int32), ("bigp", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -56,7 +56,7 @@ class PlanInfo(ctypes.Structure):
                 ("kron_w", ctypes.c_int32), ("kron_na", ctypes.c_int64), ("kron_nb", ctypes.c_int64),
                 ("kron_bits_a", ctypes.c_uint32), ("kron_bits_b", ctypes.c_uint32),
                 ("school", ctypes.c_int32), ("ks", ctypes.c_int32), ("ks_w", ctypes.c_int32),
-                ("kara", ctypes.c_int32)]
+                ("kara", ctypes.c_int32), ("bigp", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "primes"}
@@ -139,10 +139,10 @@ def _check(st: int, what: str):
         raise IpmError(st, what)
 
 
-def _params(K=0, M=0, r=0, y2=0, s=0, y1b=0, kron=0, school=0, ks=0, kara=0):
-    if not (K or M or r or y2 or s or y1b or kron or school or ks or kara):
+def _params(K=0, M=0, r=0, y2=0, s=0, y1b=0, kron=0, school=0, ks=0, kara=0, bigp=0):
+    if not (K or M or r or y2 or s or y1b or kron or school or ks or kara or bigp):
         return None
-    return Params(K, M, r, y2, s, y1b, kron, school, ks, kara)
+    return Params(K, M, r, y2, s, y1b, kron, school, ks, kara, bigp)
 
 
 def choose(na: int, nb: int, bits_a: int, bits_b: int, **overrides) -> dict:

@@ -46,17 +46,15 @@ __device__ __forceinline__ uint32_t carry_chunk(int64_t P, bool act, CarryState 
     return u - gm - ((bm >> lane) & 1u);
 }
 
-// One warp writes out = sum of nt signed terms (term i: li[i] magnitude
-// limbs at x[i], negative when neg[i]) in sign-magnitude form with lo
-// limbs; returns false when |out| is not below 2^(32 lo).  The sum is
-// carried through limb hi = max(lo, max li + 1), which holds its sign (at
-// most 16 terms, so |sum| < 2^(32 max li + 4)); limbs lo .. hi must all be
-// that sign.  lo = 0 checks that the sum is zero.
-__device__ __forceinline__ bool warp_signed_sum(const uint32_t *const *x, const int *li, const uint8_t *neg, int nt,
-                                                uint32_t *out, uint8_t *out_neg, int lo) {
+// One warp writes X = sum_q P(q) 2^(32 q) (P(q): the signed column sum of
+// limb q, |P(q)| < 2^40, zero for q > hi) in sign-magnitude form with lo
+// limbs; hi >= lo is a limb that holds X's sign.  Returns false when |X|
+// is not below 2^(32 lo): limbs lo .. hi must all be that sign, and the
+// low limbs not all zero when it is negative.  lo = 0 checks X = 0.
+template <class ColumnSum>
+__device__ __forceinline__ bool warp_sum_to_sign_magnitude(const ColumnSum &P, int hi, uint32_t *out,
+                                                           uint8_t *out_neg, int lo) {
     const int lane = threadIdx.x & 31;
-    int hi = lo;
-    for (int i = 0; i < nt; ++i) hi = max(hi, li[i] + 1);
     CarryState st;
     uint32_t sign_word = 0;
     int first_nz = -1;
@@ -64,14 +62,7 @@ __device__ __forceinline__ bool warp_signed_sum(const uint32_t *const *x, const 
     for (int q0 = 0; q0 <= hi; q0 += 32) {
         const int q = q0 + lane;
         const bool act = q <= hi;
-        int64_t P = 0;
-        if (act)
-            for (int i = 0; i < nt; ++i)
-                if (q < li[i]) {
-                    const int64_t v = (int64_t)x[i][q];
-                    P += neg[i] ? -v : v;
-                }
-        const uint32_t v = carry_chunk(P, act, st);
+        const uint32_t v = carry_chunk(act ? P(q) : 0, act, st);
         if (q < lo) out[q] = v;
         if (q == hi) sign_word = v;
         if (act && q >= lo) {
@@ -95,6 +86,25 @@ __device__ __forceinline__ bool warp_signed_sum(const uint32_t *const *x, const 
     }
     __syncwarp();
     return ok;
+}
+
+// The same for a sum of nt signed terms (term i: li[i] magnitude limbs at
+// x[i], negative when neg[i]); at most 16 terms, so the sign is settled by
+// limb max(lo, max li + 1).
+__device__ __forceinline__ bool warp_signed_sum(const uint32_t *const *x, const int *li, const uint8_t *neg, int nt,
+                                                uint32_t *out, uint8_t *out_neg, int lo) {
+    int hi = lo;
+    for (int i = 0; i < nt; ++i) hi = max(hi, li[i] + 1);
+    auto column = [&](int q) {
+        int64_t P = 0;
+        for (int i = 0; i < nt; ++i)
+            if (q < li[i]) {
+                const int64_t v = (int64_t)x[i][q];
+                P += neg[i] ? -v : v;
+            }
+        return P;
+    };
+    return warp_sum_to_sign_magnitude(column, hi, out, out_neg, lo);
 }
 
 }  // namespace ipm

@@ -71,7 +71,7 @@ ipm_status run_product(ipm_plan_s *plan, const ShapePlan &sp, const uint32_t *a,
     cudaStream_t s = (cudaStream_t)stream;
     const bool prof = plan->profiling;
     // (packed, substituted and schoolbook plans are timed as one phase)
-    if (!prof || sp.kr.s > 1 || sp.school || sp.ks.on || sp.ka.levels)
+    if (!prof || sp.kr.s > 1 || sp.school || sp.ks.on || sp.ka.levels || sp.bp.on)
         return launch_product(sp, a, an, b, bn, c, cn, stream) ? IPM_ERR_CUDA : IPM_OK;
     // profiled: events around the three passes (a split plan's outer
     // passes count with the middle one)
@@ -369,6 +369,18 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
     std::map<std::tuple<int64_t, int64_t, int32_t, int32_t>, const uint2 *> cache;
     for (auto &sp : plan->shapes) {
         if (sp.school || sp.ka.levels) continue;  // no transform tables
+        if (sp.bp.on) {  // the big prime's own tables
+            std::vector<uint64_t> words;
+            bigp_tables(sp.bp, words);
+            void *d = nullptr;
+            ce = cudaMalloc(&d, words.size() * sizeof(uint64_t));
+            if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+            plan->allocations.push_back(d);
+            ce = cudaMemcpy(d, words.data(), words.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
+            sp.bp.dtab = d;
+            continue;
+        }
         auto key = std::make_tuple(sp.kp.Y, sp.kp.Y1, sp.kp.K, sp.kp.r);
         std::vector<uint2> host((size_t)sp.kp.r * sp.table_words);
         build_tables(sp, host.data());  // also fills the scalar constants
@@ -403,10 +415,10 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
     if (flags & IPM_TENSOR_STAGES) {
         const ShapePlan *wide = nullptr;
         for (auto &sp : plan->shapes)
-            if (!sp.school && !sp.ka.levels && (!wide || sp.kp.r > wide->kp.r)) wide = &sp;
+            if (!sp.school && !sp.ka.levels && !sp.bp.on && (!wide || sp.kp.r > wide->kp.r)) wide = &sp;
         if (wide) {
             for (auto &sp : plan->shapes)
-                for (int t = 0; !sp.school && !sp.ka.levels && t < sp.kp.r; ++t)
+                for (int t = 0; !sp.school && !sp.ka.levels && !sp.bp.on && t < sp.kp.r; ++t)
                     if (sp.info.primes[t] != wide->info.primes[t]) { free_plan(plan); return IPM_ERR_UNSUPPORTED; }
             std::vector<uint32_t> frag((size_t)wide->kp.r * TC_FRAG_WORDS);
             build_tc_fragments(wide->info.primes, wide->kp.r, frag.data());
@@ -417,7 +429,7 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
             ce = cudaMemcpy(d, frag.data(), frag.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
             if (ce != cudaSuccess) { free_plan(plan); return cuda_status(ce); }
             for (auto &sp : plan->shapes)
-                if (!sp.school && !sp.ka.levels) sp.kp.tcfrag = (const uint32_t *)d;
+                if (!sp.school && !sp.ka.levels && !sp.bp.on) sp.kp.tcfrag = (const uint32_t *)d;
         }
     }
     // batched calls run a group's products at once: the workspace holds the

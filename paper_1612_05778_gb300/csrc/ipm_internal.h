@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/ipm.h"
 
 namespace ipm {
@@ -171,8 +173,31 @@ struct KaraPlan {
     size_t off_lev[KARA_MAX_LEVELS + 1], off_levn[KARA_MAX_LEVELS + 1];
 };
 
+// The big-prime form (ipm_bigp.cu): one generalized Fermat prime
+// p = (2^63 + 2^53)^2 + 1 instead of r word primes and CRT.  Elements are
+// 128-bit words; the workspace (from Z, 16-byte units) holds both operands'
+// Y x 2K arrays; the tables (device, built by the plan) hold theta^j,
+// scale theta^-j, omega_K^(+-e) and omega_Y^(+-e) at the tab_* offsets.
+struct BigpPlan {
+    int32_t on;
+    int32_t K, logK, M, N;
+    int64_t Y;
+    int32_t logY;
+    int64_t na, nb, nc;
+    int32_t la, lb, lc;
+    uint32_t bits_a, bits_b;
+    size_t off_xa, off_xb;  // in 128-bit units from Z
+    size_t tab_theta, tab_untw, tab_wk, tab_wk_i, tab_wy, tab_wy_i, table_entries;
+    uint64_t scale_lo, scale_hi, half_lo, half_hi;
+    const void *dtab;
+};
+// Tables (host, 64-bit words) and the 4H < p test of the big-prime form.
+void bigp_tables(BigpPlan &b, std::vector<uint64_t> &words);
+bool bigp_bound_ok(int64_t mn, int K, int M);
+
 struct ShapePlan {
     ipm_plan_info info;
+    BigpPlan bp;          // on = 0: not the big-prime form
     KaraPlan ka;          // levels = 0: not the Karatsuba family
     KsPlan ks;            // on = 0: not the Kronecker-substitution family
     KronPlan kr;          // s = 1: no packing (kp describes the product itself)
@@ -232,6 +257,9 @@ int launch_kara_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *a
                         const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
 int launch_school_batch(const KParams &kp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                         const uint8_t *bn, uint32_t *c, uint8_t *cn, int64_t count, void *stream);
+// The big-prime product (ipm_bigp.cu).
+int launch_bigp_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
+                        const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
 // Pack, integer product of the digit polynomials, unpack (ipm_ks.cu).
 int launch_ks_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, const uint32_t *b,
                       const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream);
@@ -247,7 +275,7 @@ int launch_school(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, con
                   uint32_t *c, uint8_t *cn, void *stream);
 // Products a batched call runs one at a time (split, packed or schoolbook).
 inline bool runs_alone(const ShapePlan &sp) {
-    return sp.school || sp.kp.Y1b > 1 || sp.kr.s > 1 || sp.ks.on || sp.ka.levels;
+    return sp.school || sp.kp.Y1b > 1 || sp.kr.s > 1 || sp.ks.on || sp.ka.levels || sp.bp.on;
 }
 int set_kernel_attributes();
 // Evaluation point for a seed, and the check c(t) = a(t) b(t) mod 2^61 - 1

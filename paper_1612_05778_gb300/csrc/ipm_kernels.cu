@@ -227,6 +227,7 @@ int launch_product(const ShapePlan &sp, const uint32_t *a, const uint8_t *an, co
                    const uint8_t *bn, uint32_t *c, uint8_t *cn, void *stream) {
     if (sp.school) return launch_school(sp, a, an, b, bn, c, cn, stream);
     if (sp.ka.levels) return launch_kara_product(sp, a, an, b, bn, c, cn, stream);
+    if (sp.bp.on) return launch_bigp_product(sp, a, an, b, bn, c, cn, stream);
     if (sp.kr.s > 1) return launch_kron_product(sp, a, an, b, bn, c, cn, stream);
     if (sp.ks.on) return launch_ks_product(sp, a, an, b, bn, c, cn, stream);
     return launch_transform_product(sp, a, an, b, bn, c, cn, stream);

@@ -459,6 +459,70 @@ ipm_status choose_plan(const ipm_shape &sh, const ipm_params *prm, ShapePlan &sp
         I.kara = 0;
         return IPM_OK;
     }
+    if (P.bigp < 0 || P.bigp > 1) return IPM_ERR_ARG;
+    if (P.bigp) {  // one generalized Fermat prime, no CRT
+        if (P.M || P.r || P.y2 || P.s || P.y1b || P.kron > 1 || P.school || P.ks || P.kara) return IPM_ERR_ARG;
+        if (P.K && (P.K < 2 || (P.K & (P.K - 1)) || P.K > (1 << KMAX_LOG2))) return IPM_ERR_ARG;
+        const int64_t mn = std::min(na, nb);
+        const uint32_t nmag = std::max(sh.bits_a, sh.bits_b);
+        const int logY = ilog2((uint64_t)kr.nc);
+        if (logY > PRIME_ORDER_LOG2) return IPM_ERR_UNSUPPORTED;
+        int K = 0, M = 0;
+        for (int logK = 1; logK <= KMAX_LOG2 && !K; ++logK) {
+            const int k = 1 << logK;
+            if (P.K && k != P.K) continue;
+            int m = (int)((nmag + 1 + k - 1) / k);
+            if (m < 2) m = 2;
+            if (m <= MMAX && bigp_bound_ok(mn, k, m)) { K = k; M = m; }
+        }
+        if (!K) return P.K ? IPM_ERR_ARG : IPM_ERR_UNSUPPORTED;
+        BigpPlan b{};
+        b.on = 1;
+        b.K = K;
+        b.logK = ilog2((uint64_t)K);
+        b.M = M;
+        b.N = K * M;
+        b.logY = logY;
+        b.Y = 1ll << logY;
+        b.na = na; b.nb = nb; b.nc = kr.nc;
+        b.la = kr.la; b.lb = kr.lb; b.lc = kr.lc;
+        b.bits_a = sh.bits_a; b.bits_b = sh.bits_b;
+        const size_t cells = (size_t)b.Y * 2 * K;  // 128-bit cells per operand
+        b.off_xa = 0;
+        b.off_xb = cells;
+        b.tab_theta = 0;
+        b.tab_untw = b.tab_theta + K;
+        b.tab_wk = b.tab_untw + K;
+        b.tab_wk_i = b.tab_wk + K / 2;
+        b.tab_wy = b.tab_wk_i + K / 2;
+        b.tab_wy_i = b.tab_wy + (size_t)(b.Y / 2);
+        b.table_entries = b.tab_wy_i + (size_t)(b.Y / 2);
+        ShapePlan s{};
+        s.school = false;
+        s.kr = kr;
+        s.bp = b;
+        s.z_words = 2 * cells * 4;
+        ipm_plan_info &I = s.info;
+        I.na = na; I.nb = nb; I.nc = kr.nc;
+        I.la = kr.la; I.lb = kr.lb; I.lc = kr.lc;
+        I.K = K; I.M = M; I.N = K * M; I.r = 1;
+        I.Y = b.Y; I.Y1 = b.Y; I.Y2 = 1; I.Y1b = 1;
+        I.log2_bound = std::log2((double)mn) + std::log2((double)K) + 2.0 * M;
+        I.log2_modulus = 126.00282;  // log2((2^63 + 2^53)^2 + 1)
+        I.kron = 1;
+        I.kron_na = na;
+        I.kron_nb = nb;
+        I.kron_bits_a = sh.bits_a;
+        I.kron_bits_b = sh.bits_b;
+        I.bigp = 1;
+        I.workspace_bytes = s.z_words * 4 + b.table_entries * 16;
+        std::memset(&s.kp, 0, sizeof(s.kp));
+        s.kp.na = na; s.kp.nb = nb; s.kp.nc = kr.nc;
+        s.kp.la = kr.la; s.kp.lb = kr.lb; s.kp.lc = kr.lc;
+        s.kp.Y1b = 1;
+        sp = s;
+        return IPM_OK;
+    }
     if (P.kara) {  // the Karatsuba family over y with schoolbook leaves
         if (P.kara > KARA_MAX_LEVELS || P.K || P.M || P.r || P.y2 || P.s || P.y1b || P.kron > 1 || P.school)
             return IPM_ERR_ARG;

@@ -238,3 +238,26 @@ def test_karatsuba_limits():
         ipm.choose(100, 100, 64, 64, kara=2, K=8)
     with pytest.raises(ipm.IpmError):
         ipm.choose(100, 100, 8192, 8192, kara=1)  # leaf columns beyond the schoolbook kernel's
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1, 1), (1024, 1024, 255, 255), (2048, 2048, 2048, 2048), (5, 9, 4096, 4096)])
+def test_big_prime_plans(shape):
+    """bigp=1: one prime p = (2^63 + 2^53)^2 + 1 (log2 p = 126.003), the
+    smallest K with N = K M >= bits + 1, M <= 62 and 4H < p."""
+    na, nb, ba, bb = shape
+    I = ipm.choose(*shape, bigp=1)
+    K, M = I["K"], I["M"]
+    mn = min(na, nb)
+    assert I["bigp"] == 1 and I["r"] == 1 and K * M == I["N"] >= max(ba, bb) + 1 and M <= 62
+    assert 4 * mn * K * 2 ** (2 * M - 2) < (2**63 + 2**53) ** 2 + 1
+    if K > 2:  # a smaller K would break the bound or M <= 62
+        k2 = K // 2
+        m2 = max(2, -(-(max(ba, bb) + 1) // k2))
+        assert m2 > 62 or 4 * mn * k2 * 2 ** (2 * m2 - 2) >= (2**63 + 2**53) ** 2 + 1
+
+
+def test_big_prime_limits():
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(100, 100, 64, 64, bigp=1, r=2)
+    with pytest.raises(ipm.IpmError):
+        ipm.choose(100, 100, 64, 64, bigp=2)

@@ -131,3 +131,61 @@ def test_result_check_catches_errors_nonzero_mod_q_and_misses_multiples_of_q():
     flipped[4] = -cq[4]
     for t in ts:
         assert _eval_mod_q(flipped, t) == _eval_mod_q(cq, t)
+
+
+# ---------------------------------------------------------------------------
+# The big-prime form (csrc/ipm_bigp.cu): arithmetic modulo the generalized
+# Fermat prime p = r^2 + 1, r = 2^63 + 2^53 (the first prime of the paper's
+# table in §3.1).
+# ---------------------------------------------------------------------------
+
+GF_R = 2**63 + 2**53
+GF_P = GF_R * GF_R + 1
+
+
+def _gf_divmod_r(x):
+    """x = q r + m: a shift by 53 and two 64-bit divisions by 1025."""
+    t = x >> 53
+    hi, lo = t >> 32, t & 0xFFFFFFFF
+    qh, rh = hi // 1025, hi % 1025
+    assert (rh << 32 | lo) < 2**64 and hi < 2**64
+    q = (qh << 32) + (rh << 32 | lo) // 1025
+    return q, x - q * GF_R
+
+
+def _gf_mul(x, y):
+    x1, x0 = _gf_divmod_r(x)
+    y1, y0 = _gf_divmod_r(y)
+    A0, A2, B = x0 * y0, x1 * y1, x0 * y1 + x1 * y0
+    assert max(x1, y1) <= GF_R < 2**64 and max(x0, y0) < GF_R and B < 2**128
+    Bq, B0 = _gf_divmod_r(B)
+    T, U = A0 + B0 * GF_R, A2 + Bq
+    assert T < 2 * GF_P < 2**128 and U < 2 * GF_P
+    T, U = T % GF_P, U % GF_P  # one conditional subtraction each
+    return (T - U) % GF_P
+
+
+def test_generalized_fermat_prime_facts():
+    assert GF_R == 1025 * 2**53
+    assert pow(3, (GF_P - 1) // 2, GF_P) == GF_P - 1  # 3 is a non-residue: 3^((p-1)/2^k) has order 2^k
+    assert (GF_P - 1) % 2**106 == 0 and ((GF_P - 1) >> 106) % 2 == 1
+    assert pow(GF_R, 2, GF_P) == GF_P - 1  # r^2 = -1: r is a primitive 4th root
+    for a in (2, 3, 5, 7, 11, 13):  # Fermat tests (the table lists p as prime)
+        assert pow(a, GF_P - 1, GF_P) == 1
+
+
+def test_divmod_by_r_and_the_folded_product():
+    rng = np.random.default_rng(126)
+    xs = [0, 1, GF_R - 1, GF_R, GF_R + 1, GF_P - 1, GF_P - 2, 2**127 - 1] + \
+         [int.from_bytes(rng.bytes(16), "little") % GF_P for _ in range(300)]
+    for x in xs:
+        q, m = _gf_divmod_r(x)
+        assert 0 <= m < GF_R and q * GF_R + m == x
+    for x in xs[:40]:
+        for y in xs[-40:]:
+            if x < GF_P and y < GF_P:
+                assert _gf_mul(x, y) == x * y % GF_P
+    big = [2**128 - 1, 2 * GF_R * (GF_R + 1) - 1]
+    for x in big:
+        q, m = _gf_divmod_r(x)
+        assert q * GF_R + m == x and m < GF_R and q < 2**66
