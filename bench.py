@@ -465,6 +465,7 @@ def measure_batch(ipm, torch, steps, warmup, plain_path, flush, rank=0, world=1,
         flags = ipm.IPM_COSTMODEL | ipm.IPM_GRAPH
     plan = ipm.Plan(tuples, flags=flags)            # the chosen form
     plan_planner = ipm.Plan(tuples)                 # batched, analytic planner
+    plan_persist = ipm.Plan(tuples, flags=flags | ipm.IPM_PERSISTENT)  # one persistent launch
     dev = [ipm.to_device(*a) + ipm.to_device(*b) for a, b in ops]
     outs = [plan.empty_output(i) for i in range(len(shapes))]
     singles = [ipm.Plan((s.na, s.nb, s.bits_a, s.bits_b)) for s in shapes]
@@ -474,8 +475,11 @@ def measure_batch(ipm, torch, steps, warmup, plain_path, flush, rank=0, world=1,
     # its pointer table to the device on every call)
     bargs = plan.batch_args(dev, outs)
     bargs_planner = plan_planner.batch_args(dev, outs)
+    outs_p = [plan_persist.empty_output(i) for i in range(len(shapes))]
+    bargs_persist = plan_persist.batch_args(dev, outs_p)
     batched = lambda: plan.mul_batched(bargs, stream=stream)  # noqa: E731
     batched_planner = lambda: plan_planner.mul_batched(bargs_planner, stream=stream)  # noqa: E731
+    batched_persist = lambda: plan_persist.mul_batched(bargs_persist, stream=stream)  # noqa: E731
     lib = ipm.load_library()
     sh = ctypes.c_void_p(int(stream.cuda_stream))
     calls = [(sp._h,) + tuple(ctypes.c_void_p(t.data_ptr()) for t in (da, dan, db, dbn, c, cn))
@@ -490,6 +494,7 @@ def measure_batch(ipm, torch, steps, warmup, plain_path, flush, rank=0, world=1,
     for _ in range(warmup):
         batched()
         batched_planner()
+        batched_persist()
         plain()
     torch.cuda.synchronize()
     plan.sync()
@@ -502,8 +507,14 @@ def measure_batch(ipm, torch, steps, warmup, plain_path, flush, rank=0, world=1,
                            torch.cuda.current_device())
     ms_p = max_over_ranks(dist, timed_ms(torch, plain, max(1, steps // 2), flush, stream),
                           torch.cuda.current_device())
+    ms_pp = max_over_ranks(dist, timed_ms(torch, batched_persist, max(1, steps // 2), flush, stream),
+                           torch.cuda.current_device())
     plan_planner.sync()
     plan.sync()
+    plan_persist.sync()
+    same_p = all(torch.equal(x[0], y[0]) and torch.equal(x[1], y[1]) for x, y in zip(outs, outs_p))
+    if not same_p:
+        raise SystemExit("the persistent launch and the grouped launches disagree")
     changed = sum(any(a[k] != b[k] for k in ("K", "M", "r", "Y2", "S", "Y1b", "kron", "school"))
                   for a, b in zip(plan.infos, plan_planner.infos))
     n = len(all_shapes)
@@ -514,6 +525,9 @@ def measure_batch(ipm, torch, steps, warmup, plain_path, flush, rank=0, world=1,
                      "path": "one ipm_mul C call per product (pointers prepared), analytic planner"},
            "batched_planner": {"ms_per_batch": ms_bp, "value": n / (ms_bp / 1e3),
                                "path": "one ipm_mul_batched call, analytic planner"},
+           "persistent": {"ms_per_batch": ms_pp, "value": n / (ms_pp / 1e3),
+                          "path": "the chosen form's plans as ONE persistent launch over a device work queue "
+                                  "(IPM_PERSISTENT, graph-replayed); outputs byte-identical"},
            "dispatch": {"flags": "IPM_COSTMODEL | IPM_GRAPH" if flags else "none (--plain)",
                         "products_with_another_plan": int(changed)},
            "workload": BATCH_WORKLOAD, "gpu_launches": int(launches), "launches_per_call": launches / steps,
@@ -522,6 +536,7 @@ def measure_batch(ipm, torch, steps, warmup, plain_path, flush, rank=0, world=1,
         sp.close()
     plan.close()
     plan_planner.close()
+    plan_persist.close()
     return res
 
 
@@ -554,7 +569,8 @@ def run_batch(args):
             "scaling": "strong" if world > 1 else "weak", "split": r["split"],
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "output_gbit_s": r["output_gbit_s"], "speedup_vs_plain": r["speedup_vs_plain"],
-            "plain": r["plain"], "batched_planner": r["batched_planner"], "dispatch": r["dispatch"],
+            "plain": r["plain"], "batched_planner": r["batched_planner"], "persistent": r["persistent"],
+            "dispatch": r["dispatch"],
             "config": {"workload": BATCH_WORKLOAD},
             "setup": {"products": r["products"], "l2": "flushed between timed steps"},
             "gpu_launches": r["gpu_launches"], "launches_per_step": r["launches_per_call"], "clocks": clocks}

@@ -82,6 +82,8 @@ typedef enum {
                                  alone); grouped batch launches keep the
                                  integer stages.  A GPU formulation of the
                                  DFTs of §2.1; the paper has no counterpart. */
+#define IPM_PERSISTENT 32u    /* batched calls run as ONE persistent launch over
+                                 a device work queue (see ipm_mul_batched) */
 #define IPM_VALIDATE 16u      /* every product is checked on the GPU after it
                                  runs (ipm_validate's test: at a fresh random
                                  point for ipm_mul and the host-buffer calls,
@@ -320,6 +322,19 @@ typedef struct {
  * graph (on a stream the plan owns; the kernels read all operand pointers
  * from the plan's device table, which every call refreshes first) and every
  * call launches that graph: one launch for all groups.
+ * With IPM_PERSISTENT, the transform and schoolbook products run instead as
+ * ONE persistent launch (two 256-thread blocks per SM when every tile fits
+ * 112 KB of shared memory, else one 512-thread block) over a device work
+ * queue of (product, phase, tile) items: each product in its own workspace
+ * slice (the plan allocates all of them: the sum of the products'
+ * workspaces), items ordered as a three-stage pipeline over windows of
+ * products, every item after the previous phase of its product, which the
+ * block awaits with a bounded device wait (ipm_set_wait_limit; a wait that
+ * runs out makes the call report IPM_ERR_TIMEOUT).  With IPM_GRAPH too,
+ * that launch is the graph.  Products that split the middle transform,
+ * pack coefficients or use another family still run one by one after it.
+ * A plan whose largest tile leaves no room in one block's shared memory
+ * for the persistent kernel keeps the grouped launches.
  */
 ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n,
                            ipm_stream_t stream);
@@ -379,6 +394,25 @@ ipm_status ipm_validate(const ipm_shape *shape, const uint32_t *a, const uint8_t
 
 /* Wait for `stream`, then return and clear the plan's device error word. */
 ipm_status ipm_sync(ipm_plan_t plan, ipm_stream_t stream);
+
+/*
+ * IPM_PERSISTENT batched plans (no counterpart in the paper): limit of every
+ * device-side dependency wait of the persistent launch, in microseconds
+ * (default 2 s, at most 600 s).  A wait that runs out sets IPM_ERR_TIMEOUT
+ * (returned by ipm_sync or by an IPM_SYNC call) and the launch returns;
+ * the outputs of that call are then incomplete.  IPM_ERR_UNSUPPORTED for a
+ * plan without the persistent launch.
+ */
+ipm_status ipm_set_wait_limit(ipm_plan_t plan, uint64_t microseconds);
+
+/*
+ * Test hook for the timeout path of IPM_PERSISTENT plans: from the next
+ * batched call on, product `product`'s forward phase counts one tile more
+ * than exists, so its later tiles wait until the limit runs out (a
+ * condition nothing satisfies); -1 removes the hold.  IPM_ERR_ARG for a
+ * product the persistent kernel does not run.
+ */
+ipm_status ipm_debug_hold(ipm_plan_t plan, int32_t product);
 
 /*
  * Taylor shift by one: g(x) = f(x + 1), exactly, for f of degree `deg`

@@ -21,6 +21,7 @@ IPM_COSTMODEL = 2
 IPM_GRAPH = 4
 IPM_TENSOR_STAGES = 8  # radix-16 stages on the INT8 tensor cores (see include/ipm.h)
 IPM_VALIDATE = 16      # every single product checked at a random point mod 2^61 - 1
+IPM_PERSISTENT = 32    # batched calls as one persistent launch over a device work queue
 
 STATUS = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_BOUND", 3: "IPM_ERR_NOMEM",
           4: "IPM_ERR_CUDA", 5: "IPM_ERR_TIMEOUT", 6: "IPM_ERR_UNSUPPORTED", 7: "IPM_ERR_MISMATCH"}
@@ -101,6 +102,8 @@ def load_library(path: str | None = None):
     lib.ipm_mul_host_async.argtypes = [V, V, V, V, V, V, V, V]
     lib.ipm_mul_batched.argtypes = [V, ctypes.POINTER(Operands), I32, V]
     lib.ipm_sync.argtypes = [V, V]
+    lib.ipm_set_wait_limit.argtypes = [V, ctypes.c_uint64]
+    lib.ipm_debug_hold.argtypes = [V, I32]
     lib.ipm_destroy.argtypes = [V]
     lib.ipm_set_profiling.argtypes = [V, I32]
     lib.ipm_phase_ms.argtypes = [V, ctypes.POINTER(ctypes.c_float), I32]
@@ -410,6 +413,16 @@ class Plan:
         """Wait for the stream and raise on a device-side error (e.g. IPM_ERR_BOUND)."""
         _check(self._lib.ipm_sync(self._h, _stream_handle(stream)), "ipm_sync")
 
+    def set_wait_limit(self, microseconds: int):
+        """IPM_PERSISTENT plans: limit of each device-side dependency wait."""
+        _check(self._lib.ipm_set_wait_limit(self._h, microseconds), "ipm_set_wait_limit")
+
+    def debug_hold(self, product: int):
+        """IPM_PERSISTENT plans, for tests of the timeout path: make product
+        `product`'s later phases wait for a tile that never exists (-1:
+        release)."""
+        _check(self._lib.ipm_debug_hold(self._h, product), "ipm_debug_hold")
+
 
 class TaylorShift:
     """g(x) = f(x + 1) for f with n coefficients below 2^bits in magnitude
@@ -539,5 +552,5 @@ def to_host(c, c_neg):
 
 
 __all__ = ["Plan", "TaylorShift", "choose", "load_library", "launch_count", "to_device", "to_host", "IpmError",
-           "IPM_SYNC", "IPM_COSTMODEL", "IPM_GRAPH", "IPM_TENSOR_STAGES", "IPM_VALIDATE", "validate", "LIB_PATH", "mul_noalloc", "output_limbs", "NOALLOC_SCRATCH_BYTES", "candidates",
+           "IPM_SYNC", "IPM_COSTMODEL", "IPM_GRAPH", "IPM_TENSOR_STAGES", "IPM_VALIDATE", "IPM_PERSISTENT", "validate", "LIB_PATH", "mul_noalloc", "output_limbs", "NOALLOC_SCRATCH_BYTES", "candidates",
            "mlp_train", "mlp_grad", "mlp_predict", "set_cost_model", "set_tuned", "dispatch"]

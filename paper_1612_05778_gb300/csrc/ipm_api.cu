@@ -37,6 +37,12 @@ struct ipm_plan_s {
     uint64_t *val_part = nullptr;
     uint64_t val_calls = 0;
     ValBatch vb;  // batched calls: the work list of their check (fixed point)
+    // IPM_PERSISTENT: one persistent launch over a device work queue
+    bool persistent = false;
+    PersistLaunch pl{};
+    std::vector<int> need_host;       // tiles per (product, phase), as built
+    int *need_dev = nullptr;
+    int hold = -1;                    // ipm_debug_hold: product whose forward phase cannot complete
     // per-pass profiling events (ipm_set_profiling)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool profiling = false;
@@ -110,6 +116,7 @@ ipm_status read_error(ipm_plan_s *plan, void *stream) {
         if (e != cudaSuccess) return cuda_status(e);
         if (h & ERRBIT_BOUND) return IPM_ERR_BOUND;
         if (h & ERRBIT_MISMATCH) return IPM_ERR_MISMATCH;
+        if (h & ERRBIT_TIMEOUT) return IPM_ERR_TIMEOUT;
         return IPM_ERR_CUDA;
     }
     return IPM_OK;
@@ -206,8 +213,12 @@ ipm_status capture_batch(ipm_plan_s *plan) {
     ce = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (ce != cudaSuccess) return cuda_status(ce);
     bool failed = false;
-    for (size_t g = 0; g < plan->batch.size(); ++g)
-        if (launch_group(plan, g, plan->capture_stream)) failed = true;
+    if (plan->persistent) {
+        if (launch_persistent(plan->pl, plan->d_ops, plan->capture_stream)) failed = true;
+    } else {
+        for (size_t g = 0; g < plan->batch.size(); ++g)
+            if (launch_group(plan, g, plan->capture_stream)) failed = true;
+    }
     cudaGraph_t g = nullptr;
     ce = cudaStreamEndCapture(plan->capture_stream, &g);
     const int captured = (int)(launches_so_far() - before);
@@ -331,6 +342,75 @@ ipm_status build_batch(ipm_plan_s *plan) {
         for (int i : g) m256 = m256 && mid256_ok(shapes[(size_t)i].kp, bl.smem[1]);
         plan->batch_mid256.push_back(m256 ? 1 : 0);
     }
+    return IPM_OK;
+}
+
+// IPM_PERSISTENT: the work list of every product the persistent kernel
+// runs (three-pass transform products and schoolbook products; the others
+// still run one by one), each transform product in its own workspace
+// slice, all of them at once.  Leaves plan->persistent false when a tile
+// needs more shared memory than the persistent kernel can take.
+ipm_status build_persistent(ipm_plan_s *plan) {
+    const auto &shapes = plan->shapes;
+    std::vector<int> members;
+    size_t words = 0, smem = 0;
+    for (int i = 0; i < (int)shapes.size(); ++i) {
+        const ShapePlan &sp = shapes[(size_t)i];
+        if (runs_alone(sp) && !sp.school) continue;
+        members.push_back(i);
+        if (sp.school) {
+            smem = std::max(smem, school_smem(sp.kp));
+        } else {
+            words += (sp.z_words + 63) & ~(size_t)63;
+            smem = std::max({smem, sp.smem_fwd, sp.smem_mid, sp.smem_inv});
+        }
+    }
+    if (members.empty() || smem > PERSIST_SMEM_MAX) return IPM_OK;
+    cudaError_t ce;
+    void *d = nullptr;
+    ce = cudaMalloc(&d, std::max<size_t>(words, 64) * sizeof(uint32_t));
+    if (ce != cudaSuccess) return cuda_status(ce);
+    plan->allocations.push_back(d);
+    uint32_t *Zp = (uint32_t *)d;
+    std::vector<KParams> params(shapes.size());
+    size_t zoff = 0;
+    for (int i : members) {
+        KParams kp = shapes[(size_t)i].kp;
+        kp.batch_index = i;
+        if (!shapes[(size_t)i].school) {
+            kp.Z = Zp + zoff;
+            zoff += (shapes[(size_t)i].z_words + 63) & ~(size_t)63;
+        }
+        params[(size_t)i] = kp;
+    }
+    std::vector<PersistSeg> segs;
+    int64_t nitems = 0;
+    persist_schedule(shapes, members, segs, plan->need_host, nitems);
+    auto upload = [&](const void *src, size_t bytes, void **dst) {
+        if ((ce = cudaMalloc(dst, bytes)) != cudaSuccess) return false;
+        plan->allocations.push_back(*dst);
+        return (ce = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice)) == cudaSuccess;
+    };
+    if (!upload(params.data(), params.size() * sizeof(KParams), &d)) return cuda_status(ce);
+    plan->pl.params = (const KParams *)d;
+    if (!upload(segs.data(), segs.size() * sizeof(PersistSeg), &d)) return cuda_status(ce);
+    plan->pl.segs = (const PersistSeg *)d;
+    if (!upload(plan->need_host.data(), plan->need_host.size() * sizeof(int), &d)) return cuda_status(ce);
+    plan->need_dev = (int *)d;
+    plan->pl.need = plan->need_dev;
+    const size_t ctl_bytes = sizeof(PersistControl) + 3 * shapes.size() * sizeof(int);
+    if ((ce = cudaMalloc(&d, ctl_bytes)) != cudaSuccess) return cuda_status(ce);
+    plan->allocations.push_back(d);
+    plan->pl.ctl = (PersistControl *)d;
+    plan->pl.done = (int *)((char *)d + sizeof(PersistControl));
+    plan->pl.ctl_bytes = ctl_bytes;
+    plan->pl.nseg = (int)segs.size();
+    plan->pl.nitems = nitems;
+    plan->pl.smem = smem;
+    if (set_kernel_attributes_persist()) return IPM_ERR_CUDA;
+    plan->pl.blocks = (unsigned)persist_blocks(smem);
+    plan->pl.wait_cycles = (long long)(PERSIST_WAIT_US_DEFAULT * 2070);  // at most 2070 cycles per microsecond
+    plan->persistent = true;
     return IPM_OK;
 }
 
@@ -459,6 +539,7 @@ ipm_status ipm_plan_ex(ipm_plan_t *out, const ipm_shape *shapes, int32_t n, uint
     }
     if (n > 1) {
         ipm_status st = build_batch(plan);
+        if (st == IPM_OK && (flags & IPM_PERSISTENT)) st = build_persistent(plan);
         if (st == IPM_OK && (flags & IPM_VALIDATE)) st = build_val_batch(plan);
         if (st != IPM_OK) { free_plan(plan); return st; }
     }
@@ -549,15 +630,18 @@ ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n, 
             ce = cudaGraphLaunch(plan->graph_exec, (cudaStream_t)stream);
             if (ce != cudaSuccess) return cuda_status(ce);
             note_launches(plan->graph_kernels);
+        } else if (plan->persistent) {
+            if (launch_persistent(plan->pl, plan->d_ops, stream)) return IPM_ERR_CUDA;
         } else {
             for (size_t g = 0; g < plan->batch.size(); ++g)
                 if (launch_group(plan, g, stream)) return IPM_ERR_CUDA;
         }
         // products whose middle transform is split or whose operands are
-        // packed run one after another
+        // packed (and, without the persistent launch, schoolbook products)
+        // run one after another
         for (int32_t i = 0; i < n; ++i) {
             const ShapePlan &sp = plan->shapes[(size_t)i];
-            if (!runs_alone(sp)) continue;
+            if (!runs_alone(sp) || (plan->persistent && sp.school)) continue;
             const ipm_operands &o = ops[i];
             if (launch_product(sp, o.a, o.a_neg, o.b, o.b_neg, o.c, o.c_neg, stream)) return IPM_ERR_CUDA;
         }
@@ -571,6 +655,33 @@ ipm_status ipm_mul_batched(ipm_plan_t plan, const ipm_operands *ops, int32_t n, 
 ipm_status ipm_sync(ipm_plan_t plan, ipm_stream_t stream) {
     if (!plan) return IPM_ERR_ARG;
     return read_error(plan, stream);
+}
+
+ipm_status ipm_set_wait_limit(ipm_plan_t plan, uint64_t microseconds) {
+    if (!plan || microseconds == 0 || microseconds > 600000000ull) return IPM_ERR_ARG;
+    if (!plan->persistent) return IPM_ERR_UNSUPPORTED;
+    plan->pl.wait_cycles = (long long)(microseconds * 2070);
+    if (plan->graph_exec) {  // the recorded launch carries the old limit: record again on the next call
+        cudaGraphExecDestroy(plan->graph_exec);
+        cudaGraphDestroy(plan->graph);
+        plan->graph_exec = nullptr;
+        plan->graph = nullptr;
+    }
+    return IPM_OK;
+}
+
+ipm_status ipm_debug_hold(ipm_plan_t plan, int32_t product) {
+    if (!plan || product < -1 || product >= (int32_t)plan->shapes.size()) return IPM_ERR_ARG;
+    if (!plan->persistent) return IPM_ERR_UNSUPPORTED;
+    std::vector<int> need = plan->need_host;
+    if (product >= 0) {
+        if (need[3 * (size_t)product] == 0) return IPM_ERR_ARG;  // not run by the persistent kernel
+        need[3 * (size_t)product] += 1;  // one forward tile more than exist: never complete
+    }
+    cudaError_t ce = cudaMemcpy(plan->need_dev, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    plan->hold = product;
+    return IPM_OK;
 }
 
 ipm_status ipm_destroy(ipm_plan_t plan) {

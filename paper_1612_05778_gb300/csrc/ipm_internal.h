@@ -66,6 +66,7 @@ __host__ __device__ inline int stage_blocks(int logL, int (&off)[8]) {
 constexpr int ERRBIT_BOUND = 1;      // an input coefficient >= 2^bits
 constexpr int ERRBIT_INTERNAL = 2;   // recombination top limb not a sign word
 constexpr int ERRBIT_MISMATCH = 4;   // IPM_VALIDATE: c(t) != a(t) b(t) mod 2^61 - 1
+constexpr int ERRBIT_TIMEOUT = 8;    // IPM_PERSISTENT: a dependency wait ran out
 
 // Randomised product check (ipm_validate.cu): blocks and threads of the
 // evaluation kernels; the scratch holds 3 x VAL_BLOCKS partial sums.
@@ -325,6 +326,42 @@ struct BatchLaunch {
     bool fwd_small, mid_tables, inv_small;
 };
 int launch_batch(const BatchLaunch &bl, const ipm_operands *ops, void *stream);
+
+// IPM_PERSISTENT (ipm_persist.cu): a batched call as one persistent launch
+// over a device work queue.  Segment = a run of consecutive items (one
+// product's tiles of one phase) starting at queue index `start`.
+constexpr size_t PERSIST_WINDOW_WORDS = (size_t)8 << 20;  // 32 MiB of workspace per pipeline window
+constexpr size_t PERSIST_SMEM_MAX = SMEM_BLOCK_MAX - 256;  // dynamic shared memory (room for the static part)
+constexpr size_t PERSIST_SMEM_SMALL = 112 * 1024;          // two 256-thread blocks per SM below this
+constexpr uint64_t PERSIST_WAIT_US_DEFAULT = 2000000;     // 2 s per dependency wait
+constexpr int PERSIST_CHUNK = 4;  // tiles per queue entry
+struct PersistSeg {
+    int64_t start;  // first queue entry (chunk) of the segment
+    int32_t product, phase, tiles, pad;
+};
+struct PersistControl {
+    unsigned long long head;  // next queue index
+    int abort;                // set when a wait timed out
+    int pad;
+};
+struct PersistLaunch {
+    const KParams *params;    // device, one per product of the plan (batch_index = product)
+    const PersistSeg *segs;   // device
+    int nseg;
+    int64_t nitems;
+    const int *need;          // device: tiles per (product, phase)
+    PersistControl *ctl;      // device: control block, then the per-(product, phase) counters
+    int *done;
+    size_t ctl_bytes;         // bytes to clear before each launch (control block and counters)
+    unsigned blocks;
+    size_t smem;
+    long long wait_cycles;
+};
+void persist_schedule(const std::vector<ShapePlan> &shapes, const std::vector<int> &members,
+                      std::vector<PersistSeg> &segs, std::vector<int> &need, int64_t &nitems);
+int persist_blocks(size_t smem);
+int set_kernel_attributes_persist();
+int launch_persistent(const PersistLaunch &pl, const ipm_operands *ops, void *stream);
 int64_t launches_so_far();
 
 }  // namespace ipm

@@ -273,7 +273,10 @@ __device__ __forceinline__ void copy_stage_tables(const KParams &P, int t, uint2
 // its own sub-block length, are copied to shared memory (else every stage
 // reads the omega_Y1 tables in global memory through the non-coherent
 // cache).
-template <bool SMTW, class TC>
+// COH: the workspace was written by other blocks of the same launch (the
+// persistent batch kernel), so it is read through L2 only: 16-byte copies
+// (cp.async.cg) or plain L2 loads, never an L1-allocating copy.
+template <bool SMTW, class TC, bool COH = false>
 __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int pb, int t) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = P.S, logS = P.logS;
@@ -317,7 +320,12 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
         } else {
             for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
                 const int i1 = e >> logS, c = e & (S - 1);
-                cp_async4(T + (size_t)padded(tmp, i1) * pitch + c, Z + base + (size_t)i1 * twoK + c);
+                uint32_t *dst = T + (size_t)padded(tmp, i1) * pitch + c;
+                const uint32_t *src = Z + base + (size_t)i1 * twoK + c;
+                if (COH)
+                    *dst = __ldcg(src);
+                else
+                    cp_async4(dst, src);
             }
         }
         cp_async_commit();
@@ -763,7 +771,9 @@ struct RowTwiddle {
 };
 
 // Pass 3 on one tile: output rows i = i1 + Y1*i2 (i2 < Y2).
-template <class TC>
+// COH: as for mid_tile (the rows were written by other blocks of the same
+// launch): plain L2 loads instead of L1-allocating asynchronous copies.
+template <class TC, bool COH = false>
 __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t *__restrict__ c,
                                          uint8_t *__restrict__ cn) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -789,7 +799,12 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
         const uint32_t *Zt = P.Z + (size_t)(t * 2) * (size_t)P.Y * twoK;
         for (int e = threadIdx.x; e < Y2 * twoK; e += blockDim.x) {
             const int pos = e >> (logK + 1), col = e & (twoK - 1);
-            cp_async4(R + (size_t)t * plane + (size_t)pos * pitch + col, Zt + ((size_t)pos * Y1 + i1) * twoK + col);
+            uint32_t *dst = R + (size_t)t * plane + (size_t)pos * pitch + col;
+            const uint32_t *src = Zt + ((size_t)pos * Y1 + i1) * twoK + col;
+            if (COH)
+                *dst = __ldcg(src);
+            else
+                cp_async4(dst, src);
         }
         const PrimeConst &pq = P.pc[t];
         uint2 *set = tw_sets + t * set_len;
