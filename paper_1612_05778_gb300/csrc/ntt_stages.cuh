@@ -24,6 +24,8 @@
 
 namespace ipm {
 
+__host__ __device__ constexpr int clog2(int x) { return x <= 1 ? 0 : 1 + clog2(x / 2); }
+
 template <int R>
 struct Roots {
     uint2 w[R / 2 > 0 ? R / 2 : 1];  // omega_R^{+-j}, j < R/2
@@ -621,8 +623,11 @@ __device__ __forceinline__ void stage_fused_pointwise(const TileMap &MA, const T
     const int lT = ilog2_if_pow2(MA.T), ltm = ilog2_if_pow2(MA.tm);
     for (int g = threadIdx.x; g < total; g += blockDim.x) {
         int blk;
-        uint32_t *ba = group_base(MA, lT, ltm, g, blk) + padded(MA, blk << LR) * MA.es;
-        uint32_t *bb = group_base(MB, lT, ltm, g, blk) + padded(MB, blk << LR) * MB.es;
+        // group_base sets blk: the offsets are added in separate statements
+        uint32_t *ba = group_base(MA, lT, ltm, g, blk);
+        ba += padded(MA, blk << LR) * MA.es;
+        uint32_t *bb = group_base(MB, lT, ltm, g, blk);
+        bb += padded(MB, blk << LR) * MB.es;
         uint32_t xa[R], xb[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) {

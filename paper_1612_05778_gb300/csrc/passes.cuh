@@ -39,7 +39,7 @@ struct FwdStore {
 };
 
 // Pass 1 on one tile: rows i = i1 + Y1*i2 (i2 < Y2) of operand op.
-template <class TC>
+template <class TC, int CK = 0, int CLY2 = 0>
 __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
                                          const uint32_t *__restrict__ a, const uint8_t *__restrict__ an,
                                          const uint32_t *__restrict__ b, const uint8_t *__restrict__ bn) {
@@ -49,8 +49,11 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
     const int64_t nX = op ? P.nb : P.na;
     const int L = op ? P.lb : P.la;
     const uint32_t bits = op ? P.bits_b : P.bits_a;
-    const int K = P.K, logK = P.logK, M = P.M;
-    const int Y2 = (int)P.Y2;
+    // CK, CLY2 > 0: the plan's K and log2 Y2 as compile-time constants (the
+    // launcher checks that they match): strides and stage radices fold
+    const int K = CK ? CK : P.K, logK = CK ? clog2(CK) : P.logK, M = P.M;
+    const int logY2 = CLY2 ? CLY2 : P.logY2;
+    const int Y2 = 1 << logY2;
     const int twoK = 2 * K;
     const int pitch = twoK + 1;  // odd row pitch: column walks hit distinct banks
     int64_t *dig = reinterpret_cast<int64_t *>(smem);            // [Y2][K]
@@ -73,8 +76,8 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
             cp_async8(set + K + Y2 + j, pq.tx_f + 2 * j);
         }
         for (int q = threadIdx.x; q < Y2; q += blockDim.x) {
-            cp_async8(set + K + q, pq.ty_f + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
-            cp_async8(set + 2 * K + Y2 + q, pq.ty_f + ((size_t)q << (P.logY - P.logY2)));
+            cp_async8(set + K + q, pq.ty_f + (size_t)i1 * bitrev((uint32_t)q, logY2));
+            cp_async8(set + 2 * K + Y2 + q, pq.ty_f + ((size_t)q << (P.logY - logY2)));
         }
         cp_async_commit();
     };
@@ -102,7 +105,6 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
     cp_async_wait<1>();  // the limbs
     __syncthreads();
     for (int i2 = warp; i2 < Y2; i2 += nw) {
-        const int64_t i = i1 + Y1 * (int64_t)i2;
         int64_t *drow = dig + (size_t)i2 * K;
         if (i2 >= nr) {
             for (int j = lane; j < K; j += 32) drow[j] = 0;
@@ -213,7 +215,7 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         //    stores row (k2, i1) -- a warp's 32 consecutive columns per row
         const TileMap ym{tile, twoK, twoK, 1, 0, pitch};
         const FwdStore out{P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK, tw_rows, (size_t)i1, (size_t)Y1, twoK, p};
-        ntt_forward_out<true>(ym, P.logY2, tw_y, P.logY2, p, p2, upper_zero, out, tc);
+        ntt_forward_out<true>(ym, logY2, tw_y, logY2, p, p2, upper_zero, out, tc);
     }
 }
 
@@ -367,16 +369,21 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
 // stored, tile i+1's second operand starts copying into the other buffer
 // while tile i+1's first operand is transformed.  Same shared memory as
 // mid_tile, same arithmetic and results.
-template <bool SMTW>
+template <bool SMTW, int CS = 0, int CLOG = 0>
 __device__ __forceinline__ void mid_tiles(const KParams &P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int S = P.S, logS = P.logS;
+    // CS, CLOG > 0: the plan's S and log2 Y1a as compile-time constants
+    // (the launcher checks that they match), so that every stride and
+    // stage radix below folds into the instructions
+    const int S = CS ? CS : P.S, logS = CS ? clog2(CS) : P.logS;
+    const int logY1a = CLOG ? CLOG : P.logY1a;
+    const int logY1 = CLOG ? CLOG : P.logY1;
     const int twoK = 2 * P.K;
-    const int Y1 = (int)P.Y1a;
+    const int Y1 = 1 << logY1a;
     uint2 *tab = reinterpret_cast<uint2 *>(smem);
     int offs[8];
-    const size_t tab_entries = (size_t)stage_blocks(P.logY1a, offs);
-    const int pl = mid_pad_log(P.logY1a, S);
+    const size_t tab_entries = (size_t)stage_blocks(logY1a, offs);
+    const int pl = mid_pad_log(logY1a, S);
     const int pitch = pl ? S : S + 1;
     const int rows = pl ? Y1 + (Y1 >> pl) : Y1;
     uint32_t *X = reinterpret_cast<uint32_t *>(SMTW ? (void *)(tab + tab_entries) : (void *)smem);
@@ -442,7 +449,7 @@ __device__ __forceinline__ void mid_tiles(const KParams &P) {
         const MidStore out{ZA + cur.base, twoK, p};
         uint32_t *q_next = Qb;
         const bool stored = ntt_convolve<SMTW, SMTW>(
-            am, bm, P.logY1a, SMTW ? tab : pc_tables_f(P, cur.t), pc_tables_i(P, cur.t), P.logY1, p, p2, pc.mont,
+            am, bm, logY1a, SMTW ? tab : pc_tables_f(P, cur.t), pc_tables_i(P, cur.t), logY1, p, p2, pc.mont,
             [] {
                 cp_async_wait<0>();
                 __syncthreads();
@@ -773,12 +780,14 @@ struct RowTwiddle {
 // Pass 3 on one tile: output rows i = i1 + Y1*i2 (i2 < Y2).
 // COH: as for mid_tile (the rows were written by other blocks of the same
 // launch): plain L2 loads instead of L1-allocating asynchronous copies.
-template <class TC, bool COH = false>
+template <class TC, bool COH = false, int CK = 0, int CLY2 = 0>
 __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t *__restrict__ c,
                                          uint8_t *__restrict__ cn) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int K = P.K, logK = P.logK, twoK = 2 * K, r = P.r, M = P.M;
-    const int Y2 = (int)P.Y2;
+    // CK, CLY2 > 0: K and log2 Y2 as compile-time constants (as fwd_tile)
+    const int K = CK ? CK : P.K, logK = CK ? clog2(CK) : P.logK, twoK = 2 * K, r = P.r, M = P.M;
+    const int logY2 = CLY2 ? CLY2 : P.logY2;
+    const int Y2 = 1 << logY2;
     const int64_t Y1 = P.Y1;
     const int pitch = twoK + 1;  // odd row pitch
     const size_t plane = (size_t)Y2 * pitch;
@@ -809,8 +818,8 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
         const PrimeConst &pq = P.pc[t];
         uint2 *set = tw_sets + t * set_len;
         for (int q = threadIdx.x; q < Y2; q += blockDim.x) {
-            cp_async8(set + q, pq.ty_i + (size_t)i1 * bitrev((uint32_t)q, P.logY2));
-            cp_async8(set + Y2 + K + q, pq.ty_i + ((size_t)q << (P.logY - P.logY2)));
+            cp_async8(set + q, pq.ty_i + (size_t)i1 * bitrev((uint32_t)q, logY2));
+            cp_async8(set + Y2 + K + q, pq.ty_i + ((size_t)q << (P.logY - logY2)));
         }
         for (int j = threadIdx.x; j < K; j += blockDim.x) cp_async8(set + Y2 + j, pq.tx_i + 2 * j);
         cp_async_commit();
@@ -838,7 +847,7 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
         // inverse y step A; its first stage applies the step-B twiddle
         // omega_Y^{-i1 k2} of row pos as it loads
         const TileMap ym{Rt, twoK, twoK, 1, 0, pitch};
-        ntt_inverse_in<true>(ym, P.logY2, tw_y, P.logY2, p, p2, RowTwiddle{tw_rows, p}, tc);
+        ntt_inverse_in<true>(ym, logY2, tw_y, logY2, p, p2, RowTwiddle{tw_rows, p}, tc);
         if (nro > 0) {
             const TileMap xm{Rt, 2 * nro, nro, pitch, K, 1};
             ntt_inverse<true>(xm, logK, tw_x, logK, p, p2, tc);
