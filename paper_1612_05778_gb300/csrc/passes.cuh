@@ -206,7 +206,10 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
         }
         __syncthreads();
         // 3. x-DFTs of length K on both halves of the non-zero rows (omega_K = theta^2)
-        if (nr > 0) {
+        if (CLY2 && nr == Y2 / 2) {  // the usual tile (half the rows hold coefficients): constant map
+            const TileMap xm{tile, Y2, Y2 / 2, pitch, K, 1};
+            ntt_forward<true>(xm, logK, tw_x, logK, p, p2, false, tc);
+        } else if (nr > 0) {
             const TileMap xm{tile, 2 * nr, nr, pitch, K, 1};
             ntt_forward<true>(xm, logK, tw_x, logK, p, p2, false, tc);
         }
@@ -848,7 +851,10 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
         // omega_Y^{-i1 k2} of row pos as it loads
         const TileMap ym{Rt, twoK, twoK, 1, 0, pitch};
         ntt_inverse_in<true>(ym, logY2, tw_y, logY2, p, p2, RowTwiddle{tw_rows, p}, tc);
-        if (nro > 0) {
+        if (CLY2 && nro == Y2) {  // every row is an output row: constant map
+            const TileMap xm{Rt, 2 * Y2, Y2, pitch, K, 1};
+            ntt_inverse<true>(xm, logK, tw_x, logK, p, p2, tc);
+        } else if (nro > 0) {
             const TileMap xm{Rt, 2 * nro, nro, pitch, K, 1};
             ntt_inverse<true>(xm, logK, tw_x, logK, p, p2, tc);
         }
