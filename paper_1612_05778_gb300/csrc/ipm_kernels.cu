@@ -44,17 +44,17 @@ void note_launches(int n) { g_launches.fetch_add(n); }
 // an SM.
 // ---------------------------------------------------------------------------
 
-template <int NT, int CK = 0, int CLY2 = 0>
+template <int NT, int CK = 0, int CLY2 = 0, int CM = 0>
 __global__ void __launch_bounds__(NT, NT == THREADS_FWD ? 3 : 1)
 k_forward(const __grid_constant__ KParams P, const uint32_t *__restrict__ a, const uint8_t *__restrict__ an,
           const uint32_t *__restrict__ b, const uint8_t *__restrict__ bn) {
-    fwd_tile<NoTc, CK, CLY2>(P, blockIdx.x, blockIdx.y, a, an, b, bn);
+    fwd_tile<NoTc, CK, CLY2, CM>(P, blockIdx.x, blockIdx.y, a, an, b, bn);
 }
 
 // persistent: one block per SM walks the tile list (passes.cuh, mid_tiles)
-template <bool SMTW, int CS = 0, int CLOG = 0>
+template <bool SMTW, int CS = 0, int CLOG = 0, int CK = 0>
 __global__ void __launch_bounds__(THREADS_MID, 1) k_middle(const __grid_constant__ KParams P) {
-    mid_tiles<SMTW, CS, CLOG>(P);
+    mid_tiles<SMTW, CS, CLOG, CK>(P);
 }
 
 // grid: x = pos * (Y1a 2K / W) + word block; y = 2t + op forward (both
@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(THREADS_OUTER) k_outer(const __grid_constant__
     outer_tile<FWD, NoTc>(P, pos, wb << P.logS2, t, op);
 }
 
-template <int NT, int CK = 0, int CLY2 = 0>
+template <int NT, int CK = 0, int CLY2 = 0, int CM = 0>
 __global__ void __launch_bounds__(NT, NT == THREADS_INV ? 2 : 1)
 k_inverse(const __grid_constant__ KParams P, uint32_t *__restrict__ c, uint8_t *__restrict__ cn) {
-    inv_tile<NoTc, false, CK, CLY2>(P, blockIdx.x, c, cn);
+    inv_tile<NoTc, false, CK, CLY2, CM>(P, blockIdx.x, c, cn);
 }
 
 template <int NT>
@@ -115,16 +115,16 @@ int set_kernel_attributes() {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
     set((const void *)k_forward<THREADS_FWD>, SMEM_FWD_MAX);
-    set((const void *)k_forward<THREADS_FWD, 32, 7>, SMEM_FWD_MAX);
-    set((const void *)k_forward<THREADS_FWD, 128, 5>, SMEM_FWD_MAX);
+    set((const void *)k_forward<THREADS_FWD, 32, 7, 33>, SMEM_FWD_MAX);
+    set((const void *)k_forward<THREADS_FWD, 128, 5, 33>, SMEM_FWD_MAX);
     set((const void *)k_forward<1024>, SMEM_FWD_MAX);
     set((const void *)k_middle<true>, SMEM_MID_MAX);
     set((const void *)k_middle<false>, SMEM_MID_MAX);
-    set((const void *)k_middle<true, 4, 12>, SMEM_MID_MAX);
-    set((const void *)k_middle<true, 8, 11>, SMEM_MID_MAX);
+    set((const void *)k_middle<true, 4, 12, 32>, SMEM_MID_MAX);
+    set((const void *)k_middle<true, 8, 11, 128>, SMEM_MID_MAX);
     set((const void *)k_inverse<THREADS_INV>, SMEM_INV_MAX);
-    set((const void *)k_inverse<THREADS_INV, 32, 7>, SMEM_INV_MAX);
-    set((const void *)k_inverse<THREADS_INV, 128, 5>, SMEM_INV_MAX);
+    set((const void *)k_inverse<THREADS_INV, 32, 7, 33>, SMEM_INV_MAX);
+    set((const void *)k_inverse<THREADS_INV, 128, 5, 33>, SMEM_INV_MAX);
     set((const void *)k_inverse<1024>, SMEM_INV_MAX);
     set((const void *)k_outer<true>, SMEM_MID_MAX);
     set((const void *)k_outer<false>, SMEM_MID_MAX);
@@ -172,10 +172,10 @@ int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint
                    const uint32_t *b, const uint8_t *bn, void *stream) {
     if (kp.tcfrag) return launch_forward_tc(kp, smem, a, an, b, bn, stream);
     dim3 grid((unsigned)kp.Y1, 2, 1);
-    if (smem <= SMEM_FWD_3PERSM && kp.K == 32 && kp.logY2 == 7)
-        k_forward<THREADS_FWD, 32, 7><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
-    else if (smem <= SMEM_FWD_3PERSM && kp.K == 128 && kp.logY2 == 5)
-        k_forward<THREADS_FWD, 128, 5><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
+    if (smem <= SMEM_FWD_3PERSM && kp.K == 32 && kp.logY2 == 7 && kp.M == 33)
+        k_forward<THREADS_FWD, 32, 7, 33><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
+    else if (smem <= SMEM_FWD_3PERSM && kp.K == 128 && kp.logY2 == 5 && kp.M == 33)
+        k_forward<THREADS_FWD, 128, 5, 33><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
     else if (smem <= SMEM_FWD_3PERSM)
         k_forward<THREADS_FWD><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
     else
@@ -215,10 +215,10 @@ int launch_middle(const KParams &kp, size_t smem, void *stream) {
     if (smem <= MID256_SMEM_MAX) return launch_middle256(kp, smem, stream);
     const unsigned grid = (unsigned)std::min(middle_tiles(kp), sm_count());
     const bool unsplit = kp.Y1b == 1 && kp.mid_tables_in_smem;
-    if (unsplit && kp.S == 4 && kp.logY1a == 12)
-        k_middle<true, 4, 12><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
-    else if (unsplit && kp.S == 8 && kp.logY1a == 11)
-        k_middle<true, 8, 11><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
+    if (unsplit && kp.S == 4 && kp.logY1a == 12 && kp.K == 32)
+        k_middle<true, 4, 12, 32><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
+    else if (unsplit && kp.S == 8 && kp.logY1a == 11 && kp.K == 128)
+        k_middle<true, 8, 11, 128><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
     else if (kp.mid_tables_in_smem)
         k_middle<true><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
     else
@@ -230,10 +230,10 @@ int launch_middle(const KParams &kp, size_t smem, void *stream) {
 int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, void *stream) {
     if (kp.tcfrag) return launch_inverse_tc(kp, smem, c, cn, stream);
     dim3 grid((unsigned)kp.Y1, 1, 1);
-    if (smem <= SMEM_INV_2PERSM && kp.K == 32 && kp.logY2 == 7)
-        k_inverse<THREADS_INV, 32, 7><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
-    else if (smem <= SMEM_INV_2PERSM && kp.K == 128 && kp.logY2 == 5)
-        k_inverse<THREADS_INV, 128, 5><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
+    if (smem <= SMEM_INV_2PERSM && kp.K == 32 && kp.logY2 == 7 && kp.M == 33)
+        k_inverse<THREADS_INV, 32, 7, 33><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
+    else if (smem <= SMEM_INV_2PERSM && kp.K == 128 && kp.logY2 == 5 && kp.M == 33)
+        k_inverse<THREADS_INV, 128, 5, 33><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
     else if (smem <= SMEM_INV_2PERSM)
         k_inverse<THREADS_INV><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
     else

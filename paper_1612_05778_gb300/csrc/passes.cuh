@@ -39,7 +39,7 @@ struct FwdStore {
 };
 
 // Pass 1 on one tile: rows i = i1 + Y1*i2 (i2 < Y2) of operand op.
-template <class TC, int CK = 0, int CLY2 = 0>
+template <class TC, int CK = 0, int CLY2 = 0, int CM = 0>
 __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
                                          const uint32_t *__restrict__ a, const uint8_t *__restrict__ an,
                                          const uint32_t *__restrict__ b, const uint8_t *__restrict__ bn) {
@@ -49,9 +49,10 @@ __device__ __forceinline__ void fwd_tile(const KParams &P, int64_t i1, int op,
     const int64_t nX = op ? P.nb : P.na;
     const int L = op ? P.lb : P.la;
     const uint32_t bits = op ? P.bits_b : P.bits_a;
-    // CK, CLY2 > 0: the plan's K and log2 Y2 as compile-time constants (the
-    // launcher checks that they match): strides and stage radices fold
-    const int K = CK ? CK : P.K, logK = CK ? clog2(CK) : P.logK, M = P.M;
+    // CK, CLY2, CM > 0: the plan's K, log2 Y2 and M as compile-time
+    // constants (the launcher checks that they match): strides, stage
+    // radices and digit positions fold into the instructions
+    const int K = CK ? CK : P.K, logK = CK ? clog2(CK) : P.logK, M = CM ? CM : P.M;
     const int logY2 = CLY2 ? CLY2 : P.logY2;
     const int Y2 = 1 << logY2;
     const int twoK = 2 * K;
@@ -372,16 +373,16 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
 // stored, tile i+1's second operand starts copying into the other buffer
 // while tile i+1's first operand is transformed.  Same shared memory as
 // mid_tile, same arithmetic and results.
-template <bool SMTW, int CS = 0, int CLOG = 0>
+template <bool SMTW, int CS = 0, int CLOG = 0, int CK = 0>
 __device__ __forceinline__ void mid_tiles(const KParams &P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    // CS, CLOG > 0: the plan's S and log2 Y1a as compile-time constants
-    // (the launcher checks that they match), so that every stride and
-    // stage radix below folds into the instructions
+    // CS, CLOG, CK > 0: the plan's S, log2 Y1a and K as compile-time
+    // constants (the launcher checks that they match), so that every
+    // stride and stage radix below folds into the instructions
     const int S = CS ? CS : P.S, logS = CS ? clog2(CS) : P.logS;
     const int logY1a = CLOG ? CLOG : P.logY1a;
     const int logY1 = CLOG ? CLOG : P.logY1;
-    const int twoK = 2 * P.K;
+    const int twoK = 2 * (CK ? CK : P.K);
     const int Y1 = 1 << logY1a;
     uint2 *tab = reinterpret_cast<uint2 *>(smem);
     int offs[8];
@@ -706,12 +707,12 @@ __device__ __forceinline__ void crt_tile(const KParams &P, uint32_t *R, size_t p
 // each by ballot carry-lookahead.  Limbs go straight to the output in two's
 // complement; a negative row is then turned into its magnitude in place (it
 // is still in L2): zero below the lowest non-zero limb f, -x at f, ~x above.
-template <int RR>
+template <int RR, int CM = 0>
 __device__ __forceinline__ void recombine_rows(const KParams &P, const uint32_t *R, int plane, int pitch,
                                                const uint4 *sources, int nro, int64_t i1,
                                                uint32_t *__restrict__ c, uint8_t *__restrict__ cn) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int lc1 = P.lc + 1, M = P.M;
+    const int lc1 = P.lc + 1, M = CM ? CM : P.M;
     const bool tab = M >= 32;
     for (int i2 = warp; i2 < nro; i2 += nw) {
         const int64_t i = i1 + P.Y1 * (int64_t)i2;
@@ -783,12 +784,12 @@ struct RowTwiddle {
 // Pass 3 on one tile: output rows i = i1 + Y1*i2 (i2 < Y2).
 // COH: as for mid_tile (the rows were written by other blocks of the same
 // launch): plain L2 loads instead of L1-allocating asynchronous copies.
-template <class TC, bool COH = false, int CK = 0, int CLY2 = 0>
+template <class TC, bool COH = false, int CK = 0, int CLY2 = 0, int CM = 0>
 __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t *__restrict__ c,
                                          uint8_t *__restrict__ cn) {
     extern __shared__ __align__(16) unsigned char smem[];
-    // CK, CLY2 > 0: K and log2 Y2 as compile-time constants (as fwd_tile)
-    const int K = CK ? CK : P.K, logK = CK ? clog2(CK) : P.logK, twoK = 2 * K, r = P.r, M = P.M;
+    // CK, CLY2, CM > 0: K, log2 Y2 and M as compile-time constants (as fwd_tile)
+    const int K = CK ? CK : P.K, logK = CK ? clog2(CK) : P.logK, twoK = 2 * K, r = P.r, M = CM ? CM : P.M;
     const int logY2 = CLY2 ? CLY2 : P.logY2;
     const int Y2 = 1 << logY2;
     const int64_t Y1 = P.Y1;
@@ -891,12 +892,12 @@ __device__ __forceinline__ void inv_tile(const KParams &P, int64_t i1, uint32_t 
     // turned into its magnitude in place (it is still in L2): zero below the
     // lowest non-zero limb f, -x at f, ~x above.
     switch (r) {
-        case 1: recombine_rows<1>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
-        case 2: recombine_rows<2>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
-        case 3: recombine_rows<3>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
-        case 4: recombine_rows<4>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
-        case 5: recombine_rows<5>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
-        default: recombine_rows<6>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        case 1: recombine_rows<1, CM>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        case 2: recombine_rows<2, CM>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        case 3: recombine_rows<3, CM>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        case 4: recombine_rows<4, CM>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        case 5: recombine_rows<5, CM>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
+        default: recombine_rows<6, CM>(P, R, (int)plane, pitch, sources, nro, i1, c, cn); break;
     }
 }
 
