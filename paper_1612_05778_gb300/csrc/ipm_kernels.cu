@@ -117,14 +117,17 @@ int set_kernel_attributes() {
     set((const void *)k_forward<THREADS_FWD>, SMEM_FWD_MAX);
     set((const void *)k_forward<THREADS_FWD, 32, 7, 33>, SMEM_FWD_MAX);
     set((const void *)k_forward<THREADS_FWD, 128, 5, 33>, SMEM_FWD_MAX);
+    set((const void *)k_forward<THREADS_FWD, 128, 5, 17>, SMEM_FWD_MAX);
     set((const void *)k_forward<1024>, SMEM_FWD_MAX);
     set((const void *)k_middle<true>, SMEM_MID_MAX);
     set((const void *)k_middle<false>, SMEM_MID_MAX);
     set((const void *)k_middle<true, 4, 12, 32>, SMEM_MID_MAX);
     set((const void *)k_middle<true, 8, 11, 128>, SMEM_MID_MAX);
+    set((const void *)k_middle<true, 16, 10, 128>, SMEM_MID_MAX);
     set((const void *)k_inverse<THREADS_INV>, SMEM_INV_MAX);
     set((const void *)k_inverse<THREADS_INV, 32, 7, 33>, SMEM_INV_MAX);
     set((const void *)k_inverse<THREADS_INV, 128, 5, 33>, SMEM_INV_MAX);
+    set((const void *)k_inverse<THREADS_INV, 128, 5, 17>, SMEM_INV_MAX);
     set((const void *)k_inverse<1024>, SMEM_INV_MAX);
     set((const void *)k_outer<true>, SMEM_MID_MAX);
     set((const void *)k_outer<false>, SMEM_MID_MAX);
@@ -176,6 +179,8 @@ int launch_forward(const KParams &kp, size_t smem, const uint32_t *a, const uint
         k_forward<THREADS_FWD, 32, 7, 33><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
     else if (smem <= SMEM_FWD_3PERSM && kp.K == 128 && kp.logY2 == 5 && kp.M == 33)
         k_forward<THREADS_FWD, 128, 5, 33><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
+    else if (smem <= SMEM_FWD_3PERSM && kp.K == 128 && kp.logY2 == 5 && kp.M == 17)
+        k_forward<THREADS_FWD, 128, 5, 17><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
     else if (smem <= SMEM_FWD_3PERSM)
         k_forward<THREADS_FWD><<<grid, THREADS_FWD, smem, (cudaStream_t)stream>>>(kp, a, an, b, bn);
     else
@@ -214,11 +219,15 @@ int launch_middle(const KParams &kp, size_t smem, void *stream) {
     // tiles small enough for two blocks per SM run in 256-thread blocks
     if (smem <= MID256_SMEM_MAX) return launch_middle256(kp, smem, stream);
     const unsigned grid = (unsigned)std::min(middle_tiles(kp), sm_count());
-    const bool unsplit = kp.Y1b == 1 && kp.mid_tables_in_smem;
-    if (unsplit && kp.S == 4 && kp.logY1a == 12 && kp.K == 32)
+    // compile-time tile shapes (with the tables in shared memory the column
+    // length log2 Y1a is the only length the stages use, split plan or not)
+    const bool tsm = kp.mid_tables_in_smem != 0;
+    if (tsm && kp.S == 4 && kp.logY1a == 12 && kp.K == 32)
         k_middle<true, 4, 12, 32><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
-    else if (unsplit && kp.S == 8 && kp.logY1a == 11 && kp.K == 128)
+    else if (tsm && kp.S == 8 && kp.logY1a == 11 && kp.K == 128)
         k_middle<true, 8, 11, 128><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
+    else if (tsm && kp.S == 16 && kp.logY1a == 10 && kp.K == 128)
+        k_middle<true, 16, 10, 128><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
     else if (kp.mid_tables_in_smem)
         k_middle<true><<<grid, THREADS_MID, smem, (cudaStream_t)stream>>>(kp);
     else
@@ -234,6 +243,8 @@ int launch_inverse(const KParams &kp, size_t smem, uint32_t *c, uint8_t *cn, voi
         k_inverse<THREADS_INV, 32, 7, 33><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
     else if (smem <= SMEM_INV_2PERSM && kp.K == 128 && kp.logY2 == 5 && kp.M == 33)
         k_inverse<THREADS_INV, 128, 5, 33><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
+    else if (smem <= SMEM_INV_2PERSM && kp.K == 128 && kp.logY2 == 5 && kp.M == 17)
+        k_inverse<THREADS_INV, 128, 5, 17><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
     else if (smem <= SMEM_INV_2PERSM)
         k_inverse<THREADS_INV><<<grid, THREADS_INV, smem, (cudaStream_t)stream>>>(kp, c, cn);
     else

@@ -381,7 +381,7 @@ __device__ __forceinline__ void mid_tiles(const KParams &P) {
     // stride and stage radix below folds into the instructions
     const int S = CS ? CS : P.S, logS = CS ? clog2(CS) : P.logS;
     const int logY1a = CLOG ? CLOG : P.logY1a;
-    const int logY1 = CLOG ? CLOG : P.logY1;
+    const int logY1 = CLOG && P.Y1b == 1 ? CLOG : P.logY1;
     const int twoK = 2 * (CK ? CK : P.K);
     const int Y1 = 1 << logY1a;
     uint2 *tab = reinterpret_cast<uint2 *>(smem);
