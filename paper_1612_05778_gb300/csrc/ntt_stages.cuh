@@ -664,16 +664,23 @@ __device__ __forceinline__ void stage_fused_pointwise(const TileMap &MA, const T
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
+// step(pass, i) runs after register stage i of the forward transform of A
+// (pass 0) or B (pass 1), and after every inverse stage i > 0 (pass 2, i
+// counting down): a caller may issue copies there.
+struct NoStep {
+    __device__ __forceinline__ void operator()(int, int) const {}
+};
 
 // after_fused() runs once B's tile is no longer read (after the pointwise
 // stage and its barrier), before the inverse stages: a caller may start
 // refilling B's memory there.
-template <bool SM, bool COMPACT, typename WaitB, class Out = TileOut, class TC = NoTc, class Hook = NoHook>
+template <bool SM, bool COMPACT, typename WaitB, class Out = TileOut, class TC = NoTc, class Hook = NoHook,
+          class Step = NoStep>
 __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &MB, int logL,
                                              const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
                                              int logT, uint32_t p, uint32_t p2, uint32_t mont, WaitB wait_b,
                                              const Out &out = Out(), const TC &tc = TC(),
-                                             const Hook &after_fused = Hook()) {
+                                             const Hook &after_fused = Hook(), const Step &step = Step()) {
     constexpr int MODE = COMPACT ? TW_STAGE : SM ? TW_SHARED : TW_GLOBAL;
     int nst, base, extra;
     stage_split(logL, nst, base, extra);
@@ -712,6 +719,7 @@ __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &M
             const int b = base + (i < extra ? 1 : 0);
             tables(toff, logLc, b, tf, ti, lg);
             run_stage<true, MODE>(b, M, logL, logLc, tf, lg, p, p2, false, tc);
+            step(pass, i);
             toff += 2 * ((1 << logLc) + (1 << b));
             logLc -= b;
         }
@@ -743,6 +751,7 @@ __device__ __forceinline__ bool ntt_convolve(const TileMap &MA, const TileMap &M
         tables(toff, logLc, b, tf, ti, lg);
         if (i > 0) {
             run_stage<false, MODE>(b, MA, logL, logLc, ti, lg, p, p2, false, tc);
+            step(2, i);
         } else {  // the last inverse stage
             const TileIn in;
             if constexpr (TC::on) {

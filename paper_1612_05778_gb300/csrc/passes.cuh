@@ -413,20 +413,32 @@ __device__ __forceinline__ void mid_tiles(const KParams &P) {
         return u;
     };
     auto slab = [&](int t, int op) { return P.Z + (size_t)(t * 2 + op) * (size_t)P.Y * twoK; };
-    auto fill = [&](uint32_t *T, const uint32_t *Z, size_t base) {
+    // rows [r0, r1) of an operand slice into a tile buffer
+    auto fill_rows = [&](uint32_t *T, const uint32_t *Z, size_t base, int r0, int r1) {
         if (copy16) {
             const int logS4 = logS - 2;
-            for (int e = threadIdx.x; e < Y1 * (S >> 2); e += blockDim.x) {
+            for (int e = threadIdx.x + (r0 << logS4); e < (r1 << logS4); e += blockDim.x) {
                 const int i1 = e >> logS4, c4 = (e & ((S >> 2) - 1)) << 2;
                 cp_async16(T + (size_t)padded(tmp, i1) * pitch + c4, Z + base + (size_t)i1 * twoK + c4);
             }
         } else {
-            for (int e = threadIdx.x; e < Y1 * S; e += blockDim.x) {
+            for (int e = threadIdx.x + (r0 << logS); e < (r1 << logS); e += blockDim.x) {
                 const int i1 = e >> logS, c = e & (S - 1);
                 cp_async4(T + (size_t)padded(tmp, i1) * pitch + c, Z + base + (size_t)i1 * twoK + c);
             }
         }
     };
+    auto fill = [&](uint32_t *T, const uint32_t *Z, size_t base) { fill_rows(T, Z, base, 0, Y1); };
+    // With three or more register stages each operand copy is issued in two
+    // halves at different stage boundaries (first operand: after the
+    // pointwise stage and after the first inverse stage; second operand: at
+    // the end of the previous tile and after the first stage of this one),
+    // so that no single point floods the load queue while the stages wait.
+    int nst_c, sbase_c, sextra_c;
+    stage_split(logY1a, nst_c, sbase_c, sextra_c);
+    const bool halves = nst_c >= 3;
+    const int half = Y1 >> 1;
+    bool b_second_half = false;  // this tile's second operand: rows [half, Y1) not yet requested
     auto load_tables = [&](int t) { copy_stage_tables(P, t, tab); };
 
     int T = blockIdx.x;
@@ -458,9 +470,21 @@ __device__ __forceinline__ void mid_tiles(const KParams &P) {
                 cp_async_wait<0>();
                 __syncthreads();
             },
-            out, NoTc(), [&] {
+            out, NoTc(),
+            [&] {
                 if (has_next) {  // the second operand is consumed: next tile's first operand into it
-                    fill(q_next, slab(nxt.t, 0), nxt.base);
+                    fill_rows(q_next, slab(nxt.t, 0), nxt.base, 0, halves ? half : Y1);
+                    cp_async_commit();
+                }
+            },
+            [&](int pass, int i) {
+                if (pass == 0 && i == 0 && b_second_half) {
+                    fill_rows(Qb, slab(cur.t, 1), cur.base, half, Y1);
+                    cp_async_commit();
+                    b_second_half = false;
+                }
+                if (pass == 2 && i == nst_c - 2 && halves && has_next) {
+                    fill_rows(q_next, slab(nxt.t, 0), nxt.base, half, Y1);
                     cp_async_commit();
                 }
             });
@@ -476,8 +500,10 @@ __device__ __forceinline__ void mid_tiles(const KParams &P) {
             load_tables(nxt.t);
             cp_async_commit();
         }
-        fill(Pb, slab(nxt.t, 1), nxt.base);  // next tile's second operand into the freed buffer
+        // next tile's second operand into the freed buffer (its first half when halved)
+        fill_rows(Pb, slab(nxt.t, 1), nxt.base, 0, halves ? half : Y1);
         cp_async_commit();
+        b_second_half = halves;
         uint32_t *tmpb = Pb;
         Pb = Qb;
         Qb = tmpb;
