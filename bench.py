@@ -892,7 +892,7 @@ def measure_product(ipm, torch, key, plain_path, steps, warmup, flush, stream, k
         del c2, cn2
     plain_plan.close()
     ms = float(np.mean(step_ms))
-    res = {"name": name, "shape": sh, "info": info, "flags": flags, "dispatch": dispatch,
+    res = {"name": name, "key": key, "shape": sh, "info": info, "flags": flags, "dispatch": dispatch,
            "step_ms": step_ms, "ms": ms, "value": 1e3 / ms, "pass_avg": pass_ms / steps,
            "plain_ms": plain_ms, "speedup_vs_plain": (plain_ms / ms) if plain_ms else 1.0,
            "launches": launches, "output_gbit_s": sh.nc * sh.lc * 32 / (ms / 1e3) / 1e9}
@@ -950,7 +950,7 @@ def product_summary(r, sm_max):
             "plain_ms": r["plain_ms"],
             "passes_ms": {PASS_NAMES[i]: float(r["pass_avg"][i]) for i in range(3)},
             "plan": {k: info[k] for k in PLAN_KEYS}, "dispatch": r["dispatch"],
-            "roofline": roofline_of(info, r["pass_avg"], sm_max)}
+            "roofline": roofline_of(info, r["pass_avg"], sm_max, traffic_workload=r["key"])}
 
 
 def run_ours(args):
