@@ -40,6 +40,9 @@ CASES = [
      dict(K=128, M=33, Y2=32, Y1=2048, S=8)),
     ((131071, 262144, 2048, 1500), dict(K=128, y2=32, s=16),
      dict(K=128, M=17, Y2=32, S=16)),
+    # one coefficient against 2^18: every forward tile of a holds at most one row
+    ((1, 262144, 1024, 1024), dict(K=32, y2=128, s=4),
+     dict(K=32, M=33, Y2=128, S=4)),
 ]
 
 
@@ -61,8 +64,8 @@ def test_instantiated_shapes_on_ragged_operands(shape, params, keys):
     lc = info["lc"]
     plan.close()
     nc = na + nb - 1
-    ks = sorted({0, 1, na - 1, na, nb - 1, nb, nc // 2, nc - 2, nc - 1,
-                 *rng.integers(0, nc, 5).tolist()})
+    ks = sorted(k for k in {0, 1, na - 1, na, nb - 1, nb, nc // 2, nc - 2, nc - 1,
+                            *rng.integers(0, nc, 5).tolist()} if 0 <= k < nc)
     want = oracle.coeffs(ks, a, b, lc)
     assert np.array_equal(got[0][ks], want[0]) and np.array_equal(got[1][ks], want[1])
     A, B, C = to_ints(*a), to_ints(*b), to_ints(*got)
@@ -71,3 +74,18 @@ def test_instantiated_shapes_on_ragged_operands(shape, params, keys):
     for q in CHECK_PRIMES:
         t = int(rng.integers(2, 2**60))
         assert oracle.eval_mod(got, t, q) == oracle.eval_mod(a, t, q) * oracle.eval_mod(b, t, q) % q
+
+
+def test_instantiated_shape_with_a_zero_operand():
+    """A zero polynomial times a full one on the bench plan's shape: every
+    output limb zero and every sign positive."""
+    sh, a, b = W.huge_dense(seed=2)
+    a = (np.zeros_like(a[0]), np.ones_like(a[1]))  # -0 everywhere
+    plan = ipm.Plan((sh.na, sh.nb, sh.bits_a, sh.bits_b), flags=ipm.IPM_SYNC, K=32, y2=128, s=4)
+    assert (plan.info["K"], plan.info["Y2"], plan.info["Y1"], plan.info["S"]) == (32, 128, 4096, 4)
+    da, dan = ipm.to_device(*a)
+    db, dbn = ipm.to_device(*b)
+    c, cn = plan.mul(da, dan, db, dbn)
+    plan.sync()
+    assert int(c.count_nonzero()) == 0 and int(cn.count_nonzero()) == 0
+    plan.close()
