@@ -39,12 +39,17 @@ constexpr int TC_FRAG_WORDS = 2048;
 // columns, one empty row after every 2^pl rows, 2^pl the radix of the last
 // stage of the length-2^logY1a column transform (the register stages split
 // log2 L into ceil(log2 L / 4) stages as evenly as possible, the last one
-// smallest); 0 (odd pitch S + 1 instead) for S >= 32.
+// smallest); 0 for S >= 32, whose rows need no padding: a warp's accesses
+// then cover whole rows.
 __host__ __device__ inline int mid_pad_log(int logY1a, int S) {
     if (S >= 32 || logY1a < 1) return 0;
     const int nst = (logY1a + 3) / 4;
     return logY1a / nst;
 }
+
+// Row pitch (words) of a middle tile: S (padded rows, or S >= 32), else the
+// odd S + 1 (a one-row column, no padding).
+__host__ __device__ inline int mid_pitch(int S, int pl) { return pl || S >= 32 ? S : S + 1; }
 
 // Offsets (uint2 entries) of the per-stage twiddle blocks of a compact
 // table for a length-2^logL transform: stage i at off[i], 2 (Lc_i + R_i)

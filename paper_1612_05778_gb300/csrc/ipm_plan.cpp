@@ -165,14 +165,14 @@ size_t inv_smem(int64_t Y2, int K, int r, int lc) {
     return (((size_t)r * Y2 * (2 * K + 1) * 4 + 15) & ~(size_t)15) + sources + tables;
 }
 // tiles of A and B (for S < 32 rows of S words with one empty row after
-// every 2^pl, else rows at pitch S + 1), plus (tables) one twiddle block per
+// every 2^pl, for S >= 32 unpadded rows of S words), plus (tables) one twiddle block per
 // register stage of the length-Y1 transform, 2 (Lc_i + R_i) entries for the
 // stage's sub-block length Lc_i and radix R_i (ntt_stages.cuh,
 // stage_blocks; passes.cuh, mid_tile)
 size_t mid_smem(int64_t Y1, int S, bool tables) {
     const int logY1 = ilog2((uint64_t)Y1);
     const int pl = mid_pad_log(logY1, S);
-    const size_t tile = pl ? (size_t)(Y1 + (Y1 >> pl)) * S : (size_t)Y1 * (S + 1);
+    const size_t tile = (size_t)(pl ? Y1 + (Y1 >> pl) : Y1) * mid_pitch(S, pl);
     size_t tab = 0;
     if (tables) {
         int off[8];

@@ -297,9 +297,9 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     // pitch S, one empty row after every R rows, R the radix of the column
     // transform's last stage (TileMap::pl) -- every stage's warp accesses
     // hit distinct banks and each row is 16-byte aligned for S >= 4.
-    // S >= 32: rows at the odd pitch S + 1.
+    // S >= 32: rows at pitch S, unpadded (a warp's accesses are whole rows).
     const int pl = mid_pad_log(P.logY1a, S);
-    const int pitch = pl ? S : S + 1;
+    const int pitch = mid_pitch(S, pl);
     const int rows = pl ? Y1 + (Y1 >> pl) : Y1;
     uint32_t *A = reinterpret_cast<uint32_t *>(SMTW ? (void *)(tab + tab_entries) : (void *)smem);
     uint32_t *B = A + (size_t)rows * pitch + 16;  // shifted 16 banks
@@ -311,11 +311,10 @@ __device__ __forceinline__ void mid_tile(const KParams &P, int cs, int pos, int 
     if (SMTW) copy_stage_tables(P, t, tab);  // copied asynchronously with A's slice
     // A's slice, then B's, as two asynchronous copy groups: B is still in
     // flight while A is transformed.  Rows of S words: 16-byte copies when
-    // both ends of every row are 16-byte aligned -- the dense padded layout
-    // (pitch S) with S a multiple of 4; row starts in global memory are
-    // multiples of 4 words from a 16-byte aligned slab -- else 4-byte
-    // copies (the odd pitch S + 1 of S >= 32 never allows 16-byte ones).
-    const bool copy16 = pl && S % 4 == 0;
+    // both ends of every row are 16-byte aligned -- pitch S with S a
+    // multiple of 4; row starts in global memory are multiples of 4 words
+    // from a 16-byte aligned slab -- else 4-byte copies.
+    const bool copy16 = pitch == S && S % 4 == 0;
     auto fill = [&](uint32_t *T, const uint32_t *Z) {
         if (copy16) {
             const int logS4 = logS - 2;
@@ -388,12 +387,12 @@ __device__ __forceinline__ void mid_tiles(const KParams &P) {
     int offs[8];
     const size_t tab_entries = (size_t)stage_blocks(logY1a, offs);
     const int pl = mid_pad_log(logY1a, S);
-    const int pitch = pl ? S : S + 1;
+    const int pitch = mid_pitch(S, pl);
     const int rows = pl ? Y1 + (Y1 >> pl) : Y1;
     uint32_t *X = reinterpret_cast<uint32_t *>(SMTW ? (void *)(tab + tab_entries) : (void *)smem);
     uint32_t *Ybuf = X + (size_t)rows * pitch + 16;
     const TileMap tmp{X, S, S, 1, 0, pitch, 0, pl};
-    const bool copy16 = pl && S % 4 == 0;
+    const bool copy16 = pitch == S && S % 4 == 0;
     const int ncs = twoK >> logS;
     const int per_t = ncs * (int)P.Y2 * (int)P.Y1b;
     const int ntiles = per_t * P.r;
