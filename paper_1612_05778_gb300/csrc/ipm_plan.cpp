@@ -220,8 +220,9 @@ bool choose_tiles(int64_t Y, int K, int r, int lc, int64_t y2_force, int s_force
             if (Y1b > 1 && Y1a > 2048) continue;
             if (Y1b > 1 && Y1a < 2) continue;
             // middle slice, with the twiddle tables in shared memory if possible
-            // (never for a split: the tables span all of Y1)
-            bool tab = Y1b == 1;
+            // (the per-stage blocks of the length-Y1a column transform, split
+            // or not)
+            bool tab = true;
             int S = tab ? widest(Y1a, true, s_force) : 0;
             if (S > 0 && S < 8 && S < 2 * K && !s_force) {
                 const int s2 = widest(Y1a, false, 0);  // wider without the tables
