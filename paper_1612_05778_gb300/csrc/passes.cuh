@@ -547,12 +547,20 @@ __device__ __forceinline__ void outer_tile(const KParams &P, int pos, size_t w0,
     const TileMap m{T, W, W, 1, 0, W};  // W transforms of length Y1b, consecutive threads on consecutive words
     TC tc{};
     tc_prime(tc, P, t);
+    // four consecutive words share i1a (w0 and 2K are multiples of 4): one
+    // twiddle per four words
     if (FWD) {
         ntt_forward(m, logY1b, pc.t1_f, P.logY1, p, p2, false, tc);
     } else {
-        for (int e = threadIdx.x; e < Y1b * W; e += blockDim.x) {
-            const int ib = e >> logW, c = e & (W - 1);
-            T[e] = shoup(T[e], tw(ib, c), p);
+        for (int e = threadIdx.x; e < Y1b * W4; e += blockDim.x) {
+            const int ib = e >> logW4, c4 = e & (W4 - 1);
+            const uint2 w = tw(ib, 4 * c4);
+            uint4 v = *reinterpret_cast<const uint4 *>(T + ib * W + 4 * c4);
+            v.x = shoup(v.x, w, p);
+            v.y = shoup(v.y, w, p);
+            v.z = shoup(v.z, w, p);
+            v.w = shoup(v.w, w, p);
+            *reinterpret_cast<uint4 *>(T + ib * W + 4 * c4) = v;
         }
         __syncthreads();
         ntt_inverse(m, logY1b, pc.t1_i, P.logY1, p, p2, tc);
@@ -561,10 +569,11 @@ __device__ __forceinline__ void outer_tile(const KParams &P, int pos, size_t w0,
         const int ib = e >> logW4, c4 = e & (W4 - 1);
         uint4 v = *reinterpret_cast<const uint4 *>(T + ib * W + 4 * c4);
         if (FWD) {
-            v.x = red(shoup(v.x, tw(ib, 4 * c4 + 0), p), p);
-            v.y = red(shoup(v.y, tw(ib, 4 * c4 + 1), p), p);
-            v.z = red(shoup(v.z, tw(ib, 4 * c4 + 2), p), p);
-            v.w = red(shoup(v.w, tw(ib, 4 * c4 + 3), p), p);
+            const uint2 w = tw(ib, 4 * c4);
+            v.x = red(shoup(v.x, w, p), p);
+            v.y = red(shoup(v.y, w, p), p);
+            v.z = red(shoup(v.z, w, p), p);
+            v.w = red(shoup(v.w, w, p), p);
         } else {
             v.x = red(v.x, p);
             v.y = red(v.y, p);
