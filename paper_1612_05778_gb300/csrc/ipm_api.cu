@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <map>
 #include <new>
@@ -320,6 +321,36 @@ ipm_status build_batch(ipm_plan_s *plan) {
             bl.smem[0] = std::max(bl.smem[0], sp.smem_fwd);
             bl.smem[1] = std::max(bl.smem[1], sp.smem_mid);
             bl.smem[2] = std::max(bl.smem[2], sp.smem_inv);
+        }
+        // forward and inverse items ordered by the (K, log2 Y2) of their
+        // product: one run per shape with a compiled kernel
+        // (ipm_kernels_batch.cu), the other shapes in one generic run
+        auto key_of = [&](uint32_t pi) -> int64_t {
+            const KParams &k = params[pi];
+            return batch_shape_compiled(k.K, k.logY2) ? (((int64_t)k.K << 8) | k.logY2) : 0;
+        };
+        for (int p : {0, 2})
+            std::stable_sort(items[p].begin(), items[p].end(),
+                             [&](const uint2 &x, const uint2 &y) { return key_of(x.x) < key_of(y.x); });
+        bl.nruns = 0;
+        for (size_t a = 0, c = 0; a < items[0].size() || c < items[2].size();) {
+            const int64_t kf = a < items[0].size() ? key_of(items[0][a].x) : INT64_MAX;
+            const int64_t ki = c < items[2].size() ? key_of(items[2][c].x) : INT64_MAX;
+            const int64_t k = std::min(kf, ki);
+            BatchRun r{};
+            r.K = (int32_t)(k >> 8);
+            r.logY2 = (int32_t)(k & 255);
+            r.f0 = (unsigned)a;
+            while (a < items[0].size() && key_of(items[0][a].x) == k) ++a;
+            r.nf = (unsigned)(a - r.f0);
+            r.i0 = (unsigned)c;
+            while (c < items[2].size() && key_of(items[2][c].x) == k) ++c;
+            r.ni = (unsigned)(c - r.i0);
+            if (bl.nruns == BATCH_RUNS_MAX) {  // more shapes than runs: one generic launch per pass
+                bl.nruns = 0;
+                break;
+            }
+            bl.runs[bl.nruns++] = r;
         }
         ce = cudaMalloc(&d, params.size() * sizeof(KParams));
         if (ce != cudaSuccess) return cuda_status(ce);

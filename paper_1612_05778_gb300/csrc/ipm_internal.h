@@ -323,14 +323,30 @@ int launch_outer_tc(const KParams &kp, size_t smem, bool forward, void *stream);
 
 // One group of a batched call: products that share the kernel variants,
 // launched as three ragged grids.  items[p][b] = (index into params, tile).
+// A run of a group's forward and inverse items whose products share (K,
+// log2 Y2): items [f0, f0 + nf) of the forward list and [i0, i0 + ni) of the
+// inverse list (K = 0: products of shapes without a compiled kernel).
+struct BatchRun {
+    int32_t K, logY2;
+    unsigned f0, nf, i0, ni;
+};
+constexpr int BATCH_RUNS_MAX = 16;
 struct BatchLaunch {
     const KParams *params;    // device array
     const uint2 *items[3];    // device arrays, one per pass
     unsigned nitems[3];
     size_t smem[3];           // largest tile of the group, per pass
     bool fwd_small, mid_tables, inv_small;
+    int32_t nruns;            // 0: one generic launch per pass
+    BatchRun runs[BATCH_RUNS_MAX];
 };
 int launch_batch(const BatchLaunch &bl, const ipm_operands *ops, void *stream);
+// ipm_kernels_batch.cu: batched forward / inverse kernels compiled for fixed
+// (K, log2 Y2)
+bool batch_shape_compiled(int K, int logY2);
+int set_kernel_attributes_batch();
+int launch_batch_run(bool fwd, int K, int logY2, const KParams *params, const ipm_operands *ops,
+                     const uint2 *items, unsigned n, size_t smem, void *stream);
 
 // IPM_PERSISTENT (ipm_persist.cu): a batched call as one persistent launch
 // over a device work queue.  Segment = a run of consecutive items (one

@@ -139,12 +139,28 @@ int set_kernel_attributes() {
     set((const void *)kb_inverse<1024>, SMEM_INV_MAX);
     if (e == cudaSuccess && set_kernel_attributes_tc()) return -1;
     if (e == cudaSuccess && set_kernel_attributes_mid256()) return -1;
+    if (e == cudaSuccess && set_kernel_attributes_batch()) return -1;
     return e == cudaSuccess ? 0 : -1;
 }
 
 int launch_batch(const BatchLaunch &bl, const ipm_operands *ops, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
-    if (bl.items[0]) {
+    if (bl.items[0] && bl.fwd_small && bl.nruns > 0) {
+        // runs of one (K, log2 Y2): compiled kernels where there is one
+        for (int k = 0; k < bl.nruns; ++k) {
+            const BatchRun &r = bl.runs[k];
+            if (!r.nf) continue;
+            const int rc = r.K ? launch_batch_run(true, r.K, r.logY2, bl.params, ops, bl.items[0] + r.f0, r.nf,
+                                                  bl.smem[0], stream)
+                               : 1;
+            if (rc < 0) return -1;
+            if (rc == 1) {
+                kb_forward<THREADS_FWD><<<r.nf, THREADS_FWD, bl.smem[0], s>>>(bl.params, ops, bl.items[0] + r.f0);
+                g_launches.fetch_add(1);
+                if (cudaGetLastError() != cudaSuccess) return -1;
+            }
+        }
+    } else if (bl.items[0]) {
         if (bl.fwd_small)
             kb_forward<THREADS_FWD><<<bl.nitems[0], THREADS_FWD, bl.smem[0], s>>>(bl.params, ops, bl.items[0]);
         else
@@ -160,7 +176,21 @@ int launch_batch(const BatchLaunch &bl, const ipm_operands *ops, void *stream) {
         g_launches.fetch_add(1);
         if (cudaGetLastError() != cudaSuccess) return -1;
     }
-    if (bl.items[2]) {
+    if (bl.items[2] && bl.inv_small && bl.nruns > 0) {
+        for (int k = 0; k < bl.nruns; ++k) {
+            const BatchRun &r = bl.runs[k];
+            if (!r.ni) continue;
+            const int rc = r.K ? launch_batch_run(false, r.K, r.logY2, bl.params, ops, bl.items[2] + r.i0, r.ni,
+                                                  bl.smem[2], stream)
+                               : 1;
+            if (rc < 0) return -1;
+            if (rc == 1) {
+                kb_inverse<THREADS_INV><<<r.ni, THREADS_INV, bl.smem[2], s>>>(bl.params, ops, bl.items[2] + r.i0);
+                g_launches.fetch_add(1);
+                if (cudaGetLastError() != cudaSuccess) return -1;
+            }
+        }
+    } else if (bl.items[2]) {
         if (bl.inv_small)
             kb_inverse<THREADS_INV><<<bl.nitems[2], THREADS_INV, bl.smem[2], s>>>(bl.params, ops, bl.items[2]);
         else
