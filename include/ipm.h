@@ -46,8 +46,9 @@
  * (128, 32, 17) in the forward and inverse passes and (S, Y1a, K) = (4,
  * 4096, 32), (8, 2048, 128) or (16, 1024, 128) in the middle pass (for
  * example d = 2^18 with 1024-bit and d = 2^15 with 4096-bit coefficients),
- * and, in batched calls, products with (K, Y2) among (16..128, 32..128)
- * pairs listed in the design notes.  ipm_get_info shows a plan's K, Y2, S.
+ * and, in the forward and inverse passes of batched calls, products with
+ * (K, Y2) = (64, 32), (64, 64), (128, 32), (32, 32), (32, 64), (32, 128),
+ * (16, 128) or (16, 64).  ipm_get_info shows a plan's K, Y2, S.
  */
 #ifndef IPM_H
 #define IPM_H
